@@ -1,0 +1,175 @@
+/*
+ * vr.h -- C ABI of libvrgpu: Vietoris-Rips persistence barcodes over Z/2 on
+ * NVIDIA B300 (sm_103a).
+ *
+ * Method: the GPU-accelerated Vietoris-Rips computation of arXiv 2502.05063,
+ * Ch. 5 ("Ripser++"): the Rips filtration of eq. 5.3 with the simplex-wise
+ * order of Sec. 5.1.4, simplices encoded by the combinatorial number system
+ * (eq. 5.6), computed dimension by dimension as cohomology (Sec. 5.2.4) with
+ * clearing (Sec. 5.2.3), filtration construction with clearing (Algorithms
+ * 17/18), apparent pairs (Def 5.3.4, Lemma 5.3.6, Algorithm 13) and a Z/2
+ * reduction of the remaining columns (Algorithm 12); dimension 0 by the
+ * minimum spanning tree (Sec. 5.2.5).
+ *
+ * Conventions shared by every entry point:
+ *  - Distances are single precision, d(i,j) = sqrt(sum_k (x_ik - x_jk)^2)
+ *    with k ascending and every operation rounded once (no fused
+ *    multiply-add), so every birth and death is an entry of that matrix.
+ *  - A p-simplex with vertices v_p > ... > v_0 has combinatorial index
+ *    cidx = sum_i C(v_i, i+1) (eq. 5.6).
+ *  - threshold = +INFINITY means "no threshold": the filtration is truncated
+ *    at the enclosing radius R = min_x max_y d(x,y) (Sec. 5.2.12,
+ *    Prop 5.2.13), which changes no pair of nonzero persistence.  A finite
+ *    threshold keeps the simplices with diam <= threshold (eq. 5.3).
+ *  - Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes; host data is copied in on `stream`.  The
+ *    library never frees caller memory.  Results are library-allocated host
+ *    memory, released with the matching *_free call.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    are synchronous with respect to the host: they return after the
+ *    results are on the host.
+ *  - On error nothing is written to *out (it is set to NULL) and the call
+ *    returns a nonzero vr_status; vr_status_string() names it.
+ *  - Every device-side wait in the library is bounded; exhausting a bound
+ *    returns VR_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef VR_H
+#define VR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VR_MAX_DIM 6 /* highest homology dimension dmax accepted */
+
+typedef enum {
+    VR_OK = 0,
+    VR_ERR_INVALID_ARG = 1,     /* bad size, NaN/negative/asymmetric distances, dmax out of range */
+    VR_ERR_OOM = 2,             /* a device or host allocation failed                              */
+    VR_ERR_INDEX_OVERFLOW = 3,  /* C(n, dmax+2) or a packed sort key does not fit 64 bits           */
+    VR_ERR_CUDA = 4,            /* a CUDA runtime call failed (no device, launch failure, ...)      */
+    VR_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out                               */
+    VR_ERR_INTERNAL = 6         /* an internal consistency check failed                             */
+} vr_status;
+
+/* flags */
+#define VR_KEEP_ZERO_LENGTH 0x1u /* also report pairs with death == birth                     */
+#define VR_CRITICAL_EDGES   0x2u /* fill vr_result.critical_edges (needed by vr_backward)     */
+
+/* One persistence pair of dimension p.  birth = diam(birth simplex),
+ * death = diam(death simplex) or +INFINITY for an essential class. */
+typedef struct {
+    float birth;
+    float death;
+    uint64_t birth_simplex; /* cidx of the birth p-simplex                         */
+    int64_t death_simplex;  /* cidx of the death (p+1)-simplex, -1 if essential    */
+} vr_pair;
+
+/* Per-dimension counters (Tables 5.1, 5.4, 5.5 of the paper report the same
+ * quantities).  For p = 0 only `candidates` (= n), `pairs`, `essential` and
+ * `emitted` are filled. */
+typedef struct {
+    int64_t candidates;  /* p-simplices enumerated, C(n, p+1)                            */
+    int64_t above_threshold; /* candidates with diam > threshold                         */
+    int64_t cleared;     /* candidates dropped by the clearing lemma                      */
+    int64_t columns;     /* columns of the coboundary matrix after threshold and clearing */
+    int64_t apparent;    /* apparent pairs found by the Apparent Pairs Lemma              */
+    int64_t reduced;     /* non-apparent columns passed to the Z/2 reduction              */
+    int64_t additions;   /* column additions performed by the reduction                   */
+    int64_t pairs;       /* persistence pairs of dimension p, zero-length included        */
+    int64_t essential;   /* classes that never die                                        */
+    int64_t emitted;     /* entries written to vr_result.pairs[p]                          */
+} vr_stats;
+
+typedef struct {
+    int32_t dmax;                       /* homology dimensions 0..dmax are reported            */
+    int64_t n;                          /* number of points                                    */
+    float threshold;                    /* threshold actually used (R when none was given)     */
+    int64_t count[VR_MAX_DIM + 1];      /* pairs per dimension                                 */
+    vr_pair* pairs[VR_MAX_DIM + 1];     /* sorted by (birth, death, birth_simplex)             */
+    int32_t* critical_edges[VR_MAX_DIM + 1]; /* if VR_CRITICAL_EDGES: 4 per pair,
+                                           (u_b, v_b, u_d, v_d) with u > v the edge attaining the
+                                           birth / death diameter (ties: largest C(u,2)+v);
+                                           u_d = v_d = -1 for essential pairs; else NULL        */
+    vr_stats stats[VR_MAX_DIM + 1];
+} vr_result;
+
+/* Barcodes of a point cloud.
+ *  pts        float[n][ambient_dim], row-major, host or device.
+ *  n          number of points, 1 <= n <= 2^20 (and C(n, dmax+2) < 2^63).
+ *  ambient_dim 1..1024.
+ *  dmax       0..VR_MAX_DIM.
+ *  threshold  see above; must not be NaN.  threshold < 0 gives an empty result.
+ *  flags      VR_* flags.
+ *  out        receives a vr_result* on success.                              */
+vr_status vr_barcodes_points(const float* pts, int64_t n, int32_t ambient_dim, int32_t dmax,
+                             float threshold, uint32_t flags, void* stream, vr_result** out);
+
+/* Barcodes of a distance matrix given as its condensed lower triangle:
+ * entry (i,j), i > j, at index i(i-1)/2 + j, n(n-1)/2 floats, host or device.
+ * Entries must be finite and >= 0 (VR_ERR_INVALID_ARG otherwise).          */
+vr_status vr_barcodes_dists(const float* lower_tri, int64_t n, int32_t dmax, float threshold,
+                            uint32_t flags, void* stream, vr_result** out);
+
+void vr_result_free(vr_result* r);
+
+/* Batched barcodes of many independent clouds (the batched form: one
+ * persistent launch over a work queue of clouds).
+ *  pts        float[sum n_i][ambient_dim], clouds stored back to back, host or device.
+ *  offsets    int64[num_clouds+1], cloud i is rows offsets[i] .. offsets[i+1]-1 (host).
+ *  Each cloud must have 1 <= n_i <= VR_BATCH_MAX_N points and dmax must be 0 or 1.
+ *  Results: for cloud i, its pairs of dimension p are
+ *  pairs[p][pair_offsets[p][i] .. pair_offsets[p][i+1]-1], sorted as above.  */
+#define VR_BATCH_MAX_N 256
+typedef struct {
+    int32_t num_clouds;
+    int32_t dmax;
+    int64_t* pair_offsets[2];           /* int64[num_clouds+1] per dimension            */
+    vr_pair* pairs[2];
+    int32_t* critical_edges[2];         /* 4 per pair if VR_CRITICAL_EDGES, else NULL   */
+    float* thresholds;                  /* float[num_clouds]: threshold used per cloud  */
+} vr_batch_result;
+
+vr_status vr_barcodes_batched(const float* pts, const int64_t* offsets, int32_t num_clouds,
+                              int32_t ambient_dim, int32_t dmax, float threshold, uint32_t flags,
+                              void* stream, vr_batch_result** out);
+void vr_batch_result_free(vr_batch_result* r);
+
+/* Backward pass: d loss / d pts given d loss / d (birth, death) of the pairs
+ * of a forward result computed with VR_CRITICAL_EDGES.  Each finite value is
+ * the length of its critical edge (u, v), so it contributes
+ * g * (x_u - x_v) / |x_u - x_v| to point u and the negative to point v.
+ *  pts        float[n][ambient_dim], device pointer.
+ *  edges      int32[num][4] (u_b, v_b, u_d, v_d), device pointer (-1 = no edge).
+ *  grad_birth, grad_death  float[num], device pointers.
+ *  grad_pts   float[n][ambient_dim], device pointer, accumulated into (+=).     */
+vr_status vr_backward(const float* pts, int64_t n, int32_t ambient_dim, const int32_t* edges,
+                      int64_t num, const float* grad_birth, const float* grad_death,
+                      float* grad_pts, void* stream);
+
+/* Vertices of the q-simplex with combinatorial index cidx among n points,
+ * written in ascending order to out_vertices[0..q].  Host-only arithmetic. */
+vr_status vr_simplex_vertices(uint64_t cidx, int32_t q, int64_t n, int32_t* out_vertices);
+
+const char* vr_status_string(vr_status s);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points, exposed so each step can be checked on its own.
+ * All pointers are device pointers; all run on `stream` and synchronise it.
+ * ---------------------------------------------------------------------- */
+
+/* Distance step: condensed lower triangle of the single-precision formula. */
+vr_status vr_distances(const float* pts, int64_t n, int32_t ambient_dim, float* out_lower_tri,
+                       void* stream);
+
+/* Radix sort of num 64-bit keys in place by their low `bits` bits (ascending,
+ * stable), values (may be NULL) permuted alongside.                          */
+vr_status vr_sort_u64(uint64_t* keys, uint64_t* values, int64_t num, int32_t bits, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VR_H */

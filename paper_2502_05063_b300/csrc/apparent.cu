@@ -1,0 +1,191 @@
+// apparent.cu -- filtration construction with clearing fused with the
+// apparent-pair search, for the p-simplices of one dimension.
+//
+// Paper (arXiv 2502.05063): Algorithm 17 keeps a p-simplex s iff it is not
+// the death simplex of a (p-1)-pair (clearing lemma, Sec. 5.2.3) and
+// diam(s) <= threshold; Algorithm 18 launches one thread per candidate
+// index and sorts the kept columns; Algorithm 13 then tests each column with
+// the Apparent Pairs Lemma (Lemma 5.3.6): t is the first cofacet of s, in
+// decreasing combinatorial index, with diam(t) = diam(s), and no facet s' of
+// t with diam(s') = diam(s) has a smaller index than s.  By Cor 5.3.7 the
+// test is independent per column and by Prop 5.3.9 it may run after
+// clearing.
+//
+// B300 design (differs from the paper's thread-per-column kernel):
+//  * no sort of the kept columns: the apparent test does not need the
+//    coboundary order, so filtering and the search run in one kernel and
+//    only the non-apparent columns (about 1% of them) are written out, as
+//    packed (rank, index) keys for the later radix sort;
+//  * candidates are taken 32 consecutive indices per warp (one per lane,
+//    each lane decodes its own simplex from the combinatorial number system
+//    of eq. 5.6), and the cofacet search of each kept candidate is
+//    warp-cooperative: the lanes test 32 consecutive added vertices w at
+//    once (w descending = cofacet index descending), reading row v_i of the
+//    symmetric rank matrix at columns w..w-31 -- one coalesced 128-byte load
+//    per vertex of s -- and a ballot picks the largest qualifying w;
+//  * the facet test needs only the ranks among the p+2 vertices of t, one
+//    pair per lane, and a ballot per vertex of s above w.
+// Apparent pairs have zero persistence (diam(s) = diam(t)); they are only
+// counted, marked in the clearing bitmap of dimension p+1, and written out
+// when zero-length pairs are requested.
+#include "vr_common.cuh"
+
+namespace vr {
+
+namespace {
+
+// pair index k of a (Q)-vertex set -> (i, j), i > j
+__device__ __forceinline__ void pair_of(int k, int& i, int& j) {
+    i = 1;
+    while (k >= i) { k -= i; ++i; }
+    j = k;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256)
+k_filtration_apparent(RankMatrix R, Binom B, uint32_t thr, const uint32_t* __restrict__ clear_bits,
+                      int cidx_bits, uint64_t rmask, uint64_t num_cand, ApparentOut o) {
+    constexpr int NV = P + 1;                 // vertices of s
+    constexpr int NPAIR_T = (P + 2) * (P + 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t n = R.n;
+    unsigned long long c_above = 0, c_cleared = 0, c_kept = 0, c_app = 0;
+
+    for (uint64_t chunk = warp; chunk * 32 < num_cand; chunk += nwarps) {
+        const uint64_t c = chunk * 32 + lane;
+        int v[NV];
+        uint32_t r = 0;
+        bool kept = false;
+        if (c < num_cand) {
+            decode_simplex<P>(B, c, n - 1, v);
+#pragma unroll
+            for (int a = 1; a < NV; ++a)
+#pragma unroll
+                for (int b = 0; b < a; ++b) r = max(r, R(v[a], v[b]));
+            if (r > thr) ++c_above;
+            else if (clear_bits && ((__ldg(clear_bits + (c >> 5)) >> (c & 31)) & 1u)) ++c_cleared;
+            else { kept = true; ++c_kept; }
+        }
+        uint32_t kmask = __ballot_sync(0xffffffffu, kept);
+        while (kmask) {
+            const int src = __ffs(kmask) - 1;
+            kmask &= kmask - 1;
+            int sv[NV];
+#pragma unroll
+            for (int a = 0; a < NV; ++a) sv[a] = __shfl_sync(0xffffffffu, v[a], src);
+            const uint32_t sr = __shfl_sync(0xffffffffu, r, src);
+            const uint64_t sc = __shfl_sync(0xffffffffu, c, src);
+            // first cofacet in decreasing index with the same diameter
+            int64_t wf = -1;
+            for (int64_t base = n - 1; base >= 0; base -= 32) {
+                const int64_t w = base - lane;
+                bool ok = w >= 0;
+#pragma unroll
+                for (int a = 0; a < NV; ++a) ok = ok && (w != sv[a]);
+#pragma unroll
+                for (int a = 0; a < NV; ++a) ok = ok && (R(sv[a], w) <= sr);
+                const uint32_t b = __ballot_sync(0xffffffffu, ok);
+                if (b) { wf = base - (__ffs(b) - 1); break; }
+            }
+            bool apparent = false;
+            if (wf >= 0) {
+                // t = s + wf; lane k tests pair k of t for rank == diam
+                int tv[NV + 1];
+#pragma unroll
+                for (int a = 0; a < NV; ++a) tv[a] = sv[a];
+                tv[NV] = (int)wf;
+                bool eq = false;
+                int pi = 0, pj = 0;
+                if (lane < NPAIR_T) {
+                    pair_of(lane, pi, pj);
+                    eq = R(tv[pi], tv[pj]) == sr;
+                }
+                apparent = true;
+#pragma unroll
+                for (int a = 0; a < NV; ++a) {
+                    if (sv[a] > wf) {  // facet t \ {sv[a]} has a smaller index than s
+                        const bool avoid = eq && pi != a && pj != a;
+                        if (__ballot_sync(0xffffffffu, avoid)) apparent = false;
+                    }
+                }
+            }
+            if (lane == 0) {
+                if (apparent) {
+                    ++c_app;
+                    if (o.clear_next || o.zero_pairs) {
+                        // index of t: insert wf into the ascending vertices of s
+                        uint64_t ct = 0;
+                        int k = 0;
+                        bool placed = false;
+                        for (int a = 0; a < NV; ++a) {
+                            if (!placed && wf < sv[a]) { ct += B(wf, k + 1); ++k; placed = true; }
+                            ct += B(sv[a], k + 1);
+                            ++k;
+                        }
+                        if (!placed) ct += B(wf, k + 1);
+                        if (o.clear_next) atomicOr(o.clear_next + (ct >> 5), 1u << (ct & 31));
+                        if (o.zero_pairs) {
+                            unsigned long long at = atomicAdd(o.num_zero_pairs, 1ull);
+                            PairRec pr;
+                            pr.birth_rank = sr; pr.death_rank = sr;
+                            pr.birth_cidx = sc; pr.death_cidx = (int64_t)ct;
+                            o.zero_pairs[at] = pr;
+                        }
+                    }
+                } else {
+                    unsigned long long at = atomicAdd(o.num_nonapparent, 1ull);
+                    if ((int64_t)at < o.capacity)
+                        o.nonapparent_keys[at] = ((~(uint64_t)sr & rmask) << cidx_bits) | sc;
+                    else
+                        atomicExch(o.dev_err, DEV_CAPACITY);
+                }
+            }
+        }
+    }
+    // counters
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        c_above += __shfl_xor_sync(0xffffffffu, c_above, off);
+        c_cleared += __shfl_xor_sync(0xffffffffu, c_cleared, off);
+        c_kept += __shfl_xor_sync(0xffffffffu, c_kept, off);
+    }
+    if (lane == 0) {
+        if (c_above) atomicAdd(o.counters + 0, c_above);
+        if (c_cleared) atomicAdd(o.counters + 1, c_cleared);
+        if (c_kept) atomicAdd(o.counters + 2, c_kept);
+        if (c_app) atomicAdd(o.counters + 3, c_app);
+    }
+}
+
+template <int P>
+void launch_p(const RankMatrix& R, const Binom& B, uint32_t thr, const uint32_t* clear_bits, int cidx_bits,
+              uint64_t rmask, uint64_t num_cand, const ApparentOut& o, cudaStream_t s) {
+    const uint64_t chunks = (num_cand + 31) / 32;
+    uint64_t blocks = (chunks + 7) / 8;
+    const uint64_t cap = 148ull * 8;  // 8 resident 256-thread blocks per SM
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_filtration_apparent<P><<<(unsigned)blocks, 256, 0, s>>>(R, B, thr, clear_bits, cidx_bits, rmask, num_cand, o);
+    VR_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void launch_filtration_apparent(int p, const RankMatrix& R, const Binom& B, uint32_t thr_rank,
+                                const uint32_t* clear_bits, int cidx_bits, int rank_bits, uint64_t num_cand,
+                                const ApparentOut& o, cudaStream_t s) {
+    const uint64_t rmask = rank_bits >= 64 ? ~0ull : ((1ull << rank_bits) - 1);
+    switch (p) {
+        case 1: launch_p<1>(R, B, thr_rank, clear_bits, cidx_bits, rmask, num_cand, o, s); break;
+        case 2: launch_p<2>(R, B, thr_rank, clear_bits, cidx_bits, rmask, num_cand, o, s); break;
+        case 3: launch_p<3>(R, B, thr_rank, clear_bits, cidx_bits, rmask, num_cand, o, s); break;
+        case 4: launch_p<4>(R, B, thr_rank, clear_bits, cidx_bits, rmask, num_cand, o, s); break;
+        case 5: launch_p<5>(R, B, thr_rank, clear_bits, cidx_bits, rmask, num_cand, o, s); break;
+        case 6: launch_p<6>(R, B, thr_rank, clear_bits, cidx_bits, rmask, num_cand, o, s); break;
+        default: throw Error{VR_ERR_INVALID_ARG};
+    }
+}
+
+}  // namespace vr

@@ -1,0 +1,172 @@
+// radix_sort.cu -- least-significant-digit radix sort on packed integer keys.
+//
+// The filtration must be put in coboundary order, decreasing diameter then
+// increasing combinatorial index (Algorithm 18, Sec. 5.5.2 of the paper);
+// the keys packed by the callers make that order the ascending order of an
+// unsigned integer, and only the significant low bits are sorted.
+//
+// One pass per 8-bit digit, three kernels per pass, no inter-block waits:
+//   1. k_hist    per-tile digit histogram, stored digit-major
+//   2. k_scan    exclusive scan of the (digit, tile) counts in one block
+//   3. k_scatter stable scatter: a tile is walked in index order, ranks of
+//                equal digits inside a warp come from __match_any_sync, the
+//                offsets of earlier warps and rounds from shared counters.
+#include "vr_common.cuh"
+
+namespace vr {
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ROUNDS = 16;                       // items per thread
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;     // 4096 keys per tile
+constexpr int RS_BINS = 256;
+
+template <class K>
+__global__ void k_hist(const K* __restrict__ keys, int64_t num, int shift, uint32_t* __restrict__ hist,
+                       int64_t tiles) {
+    __shared__ uint32_t bins[RS_BINS];
+    for (int b = threadIdx.x; b < RS_BINS; b += blockDim.x) bins[b] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t idx = base + (int64_t)r * RS_THREADS + threadIdx.x;
+        if (idx < num) atomicAdd(&bins[(uint32_t)(keys[idx] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < RS_BINS; b += blockDim.x) hist[(int64_t)b * tiles + blockIdx.x] = bins[b];
+}
+
+// Exclusive scan of cnt[0..len) in place, one block of 1024 threads.
+__global__ void k_scan(uint32_t* __restrict__ cnt, int64_t len) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < len; base += blockDim.x) {
+        int64_t idx = base + threadIdx.x;
+        uint32_t x = idx < len ? cnt[idx] : 0;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+            uint32_t ti = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+                if (lane >= o) ti += y;
+            }
+            warp_tot[lane] = ti - t;  // exclusive over warps
+        }
+        __syncthreads();
+        uint32_t c0 = carry;
+        if (idx < len) cnt[idx] = c0 + warp_tot[wid] + incl - x;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = c0 + warp_tot[wid] + incl;
+        __syncthreads();
+    }
+}
+
+template <class K, class V, bool HAS_V>
+__global__ void k_scatter(const K* __restrict__ kin, const V* __restrict__ vin, K* __restrict__ kout,
+                          V* __restrict__ vout, int64_t num, int shift, const uint32_t* __restrict__ offs,
+                          int64_t tiles) {
+    __shared__ uint32_t base_off[RS_BINS];         // global start of each digit for this tile
+    __shared__ uint32_t running[RS_BINS];          // items of each digit already placed
+    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];   // this round: items per warp and digit
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b = threadIdx.x; b < RS_BINS; b += blockDim.x) {
+        base_off[b] = offs[(int64_t)b * tiles + blockIdx.x];
+        running[b] = 0;
+        for (int w = 0; w < RS_WARPS; ++w) wcnt[w][b] = 0;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t idx = base + (int64_t)r * RS_THREADS + threadIdx.x;
+        bool valid = idx < num;
+        K key = valid ? kin[idx] : (K)0;
+        V val = (HAS_V && valid) ? vin[idx] : (V)0;
+        uint32_t d = valid ? ((uint32_t)(key >> shift) & 0xFF) : (uint32_t)(RS_BINS + lane);
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t lrank = __popc(peers & lt_mask);
+        if (valid && lrank == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        for (int b = threadIdx.x; b < RS_BINS; b += blockDim.x) {
+            uint32_t acc = running[b];
+            for (int w = 0; w < RS_WARPS; ++w) {
+                uint32_t c = wcnt[w][b];
+                wcnt[w][b] = acc;  // becomes the warp's offset for this round
+                acc += c;
+            }
+            running[b] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = base_off[d] + wcnt[wid][d] + lrank;
+            kout[pos] = key;
+            if (HAS_V) vout[pos] = val;
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < RS_BINS; b += blockDim.x)
+            for (int w = 0; w < RS_WARPS; ++w) wcnt[w][b] = 0;
+        __syncthreads();
+    }
+}
+
+template <class K, class V, bool HAS_V>
+void radix_sort_impl(Workspace& ws, K* keys, V* vals, int64_t num, int bits) {
+    if (num <= 1 || bits <= 0) return;
+    VR_CHECK(num < (int64_t)UINT32_MAX, VR_ERR_INVALID_ARG);
+    const int64_t tiles = (num + RS_TILE - 1) / RS_TILE;
+    K* kalt = ws.alloc_n<K>(num);
+    V* valt = HAS_V ? ws.alloc_n<V>(num) : nullptr;
+    uint32_t* hist = ws.alloc_n<uint32_t>(tiles * RS_BINS);
+    K* kin = keys; K* kout = kalt;
+    V* vin = vals; V* vout = valt;
+    const int passes = (bits + 7) / 8;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = ps * 8;
+        k_hist<K><<<(unsigned)tiles, RS_THREADS, 0, ws.stream>>>(kin, num, shift, hist, tiles);
+        k_scan<<<1, 1024, 0, ws.stream>>>(hist, tiles * RS_BINS);
+        k_scatter<K, V, HAS_V><<<(unsigned)tiles, RS_THREADS, 0, ws.stream>>>(kin, vin, kout, vout, num, shift,
+                                                                               hist, tiles);
+        VR_CUDA(cudaGetLastError());
+        K* tk = kin; kin = kout; kout = tk;
+        V* tv = vin; vin = vout; vout = tv;
+    }
+    if (kin != keys) {
+        VR_CUDA(cudaMemcpyAsync(keys, kin, num * sizeof(K), cudaMemcpyDeviceToDevice, ws.stream));
+        if (HAS_V) VR_CUDA(cudaMemcpyAsync(vals, vin, num * sizeof(V), cudaMemcpyDeviceToDevice, ws.stream));
+    }
+}
+
+}  // namespace
+
+void radix_sort_u64(Workspace& ws, uint64_t* keys, uint64_t* vals, int64_t num, int bits) {
+    if (vals) radix_sort_impl<uint64_t, uint64_t, true>(ws, keys, vals, num, bits);
+    else radix_sort_impl<uint64_t, uint64_t, false>(ws, keys, nullptr, num, bits);
+}
+
+void scan_u32_exclusive(uint32_t* data, int64_t num, cudaStream_t s) {
+    if (num <= 0) return;
+    k_scan<<<1, 1024, 0, s>>>(data, num);
+    VR_CUDA(cudaGetLastError());
+}
+
+void radix_sort_u32(Workspace& ws, uint32_t* keys, uint32_t* vals, int64_t num, int bits) {
+    if (vals) radix_sort_impl<uint32_t, uint32_t, true>(ws, keys, vals, num, bits);
+    else radix_sort_impl<uint32_t, uint32_t, false>(ws, keys, nullptr, num, bits);
+}
+
+}  // namespace vr

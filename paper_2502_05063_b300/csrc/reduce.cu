@@ -1,0 +1,603 @@
+// reduce.cu -- Z/2 reduction of the non-apparent columns of the coboundary
+// matrix (paper: Algorithm 12, oblivious column reduction, Lemma 5.2.10;
+// cohomology, Sec. 5.2.4; implicit matrix, Sec. 5.2.8; two-layer pair store,
+// Sec. 5.5.1).
+//
+// Rows are (p+1)-simplices identified by a 64-bit row key
+//     (diameter rank << row_cidx_bits) | (row_mask - cidx),
+// so the pivot ("low") of a column -- the cofacet first in the simplex-wise
+// filtration order -- is its smallest row key.  A column is the sum over Z/2
+// of the coboundaries D_x of a set of p-simplices; D_x is never stored but
+// generated from the vertices of x (one lane per added vertex w).
+//
+// Parallel schedule (B300 design; the paper reduces these columns
+// sequentially on the CPU).  Columns c_0 < c_1 < ... are in coboundary
+// order.  Each round, every unfinished column is reduced independently
+// against the pivots known so far (apparent pairs + finalized columns) until
+// its pivot is unknown, or a per-round budget of additions runs out.  Then,
+// in order, column j is finalized iff its reduction completed and its pivot
+// key is smaller than the current pivot key of every earlier unfinished
+// column.  This is exact: the finished low of column i is the smallest low
+// over D_i + span(D_<i), so every partial state of i bounds its final pivot
+// key from below; a pivot key of j below all those bounds cannot be the
+// final pivot of any earlier column, and a vector of D_j + span(D_<j) whose
+// low is no earlier column's pivot has the low of the fully reduced column
+// (the argument behind Lemma 5.2.10).  Columns finalized in one round have
+// strictly decreasing keys, hence distinct pivots.  When a round makes no
+// progress or few columns remain, one warp finishes them in order, which is
+// Algorithm 12 verbatim.
+//
+// Pivot lookup (the paper's two-layer store, Fig 5.10): first a device hash
+// of pivots found by this reduction, then the apparent pairs, which are not
+// stored at all: t is owned by an apparent column iff its youngest facet s'
+// (drop the largest vertex whose removal keeps diam) has t as its oldest
+// cofacet (no larger added vertex keeps diam) -- Def 5.3.4 evaluated on the
+// fly in one warp.  No wait in this file spins on another thread.
+#include "vr_common.cuh"
+
+namespace vr {
+
+namespace {
+
+constexpr uint64_t EMPTY = ~0ull;
+constexpr int RED_WARPS = 4;      // warps per block, round mode
+constexpr int STAGE = 1024;       // per-warp shared staging of generated rows
+constexpr uint8_t ST_COMPLETE = 0, ST_BUDGET = 1, ST_OVERFLOW = 2;
+
+struct Ctx {
+    RankMatrix R;
+    Binom B;
+    uint32_t thr;
+    int cb, rcb;
+    uint64_t cmask, rcmask, rmask;
+    const uint64_t* cols;
+    int64_t num_cols;
+    uint64_t* hkeys;   // pivot cidx (EMPTY = free)
+    uint32_t* hvals;   // column position
+    uint64_t hmask;
+    int* err;
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull; x ^= x >> 33;
+    return x;
+}
+
+template <int P>
+struct Simplex {
+    int v[P + 1];   // ascending
+    uint32_t r;     // diameter rank
+    uint64_t cidx;
+};
+
+template <int P>
+__device__ __forceinline__ void load_col(const Ctx& c, uint64_t key, Simplex<P>& s) {
+    s.cidx = key & c.cmask;
+    s.r = (uint32_t)((~(key >> c.cb)) & c.rmask);
+    decode_simplex<P>(c.B, s.cidx, c.R.n - 1, s.v);
+}
+
+template <int P>
+__device__ __forceinline__ uint64_t col_key(const Ctx& c, const Simplex<P>& s) {
+    return ((~(uint64_t)s.r & c.rmask) << c.cb) | s.cidx;
+}
+
+// index of s + {w}, w not a vertex of s (eq. 5.6 with w inserted in place)
+template <int P>
+__device__ __forceinline__ uint64_t cofacet_cidx(const Binom& B, const int* v, int64_t w) {
+    uint64_t ct = 0;
+    int k = 0;
+    bool placed = false;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+        if (!placed && w < v[a]) { ct += B(w, k + 1); ++k; placed = true; }
+        ct += B(v[a], k + 1);
+        ++k;
+    }
+    if (!placed) ct += B(w, k + 1);
+    return ct;
+}
+
+template <int P>
+__device__ __forceinline__ uint64_t row_key(const Ctx& c, const Simplex<P>& s, int64_t w, uint32_t rt) {
+    return ((uint64_t)rt << c.rcb) | (c.rcmask - cofacet_cidx<P>(c.B, s.v, w));
+}
+
+// Pivot of the unreduced column D_s: smallest (rank asc, w desc) cofacet.
+template <int P>
+__device__ uint64_t warp_column_pivot(const Ctx& c, const Simplex<P>& s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = c.R.n;
+    uint32_t brt = 0xFFFFFFFFu;
+    int64_t bw = -1;
+    for (int64_t base = n - 1; base >= 0; base -= 32) {
+        const int64_t w = base - lane;
+        bool ok = w >= 0;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) ok = ok && (w != s.v[a]);
+        if (ok) {
+            uint32_t rt = s.r;
+#pragma unroll
+            for (int a = 0; a <= P; ++a) rt = max(rt, c.R(s.v[a], w));
+            if (rt <= c.thr && rt < brt) { brt = rt; bw = w; }  // w only decreases per lane
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint32_t ort = __shfl_xor_sync(0xffffffffu, brt, o);
+        int64_t ow = __shfl_xor_sync(0xffffffffu, bw, o);
+        if (ort < brt || (ort == brt && ow > bw)) { brt = ort; bw = ow; }
+    }
+    if (bw < 0) return EMPTY;
+    return row_key<P>(c, s, bw, brt);
+}
+
+// Bitonic sort of stage[0..len) (len a power of two >= 32) by one warp.
+__device__ void warp_bitonic(uint64_t* stage, int len) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= len; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < len; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t a = stage[i], b = stage[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { stage[i] = b; stage[ixj] = a; }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t len, uint64_t x) {
+    int64_t lo = 0, hi = len;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// out = in XOR S (symmetric difference of two sorted sets), returns the new
+// size or -1 if it would exceed cap.
+__device__ int64_t warp_xor_merge(const uint64_t* in, int64_t a, const uint64_t* S, int b, uint64_t* out,
+                                  int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    int64_t matched = 0;
+    bool over = false;
+    for (int64_t base = 0; base < a; base += 32) {
+        const int64_t i = base + lane;
+        const uint64_t x = i < a ? in[i] : EMPTY;
+        int64_t bs = 0;
+        bool m = false;
+        if (i < a) {
+            bs = lower_bound_u64(S, b, x);
+            m = bs < b && S[bs] == x;
+        }
+        const uint32_t mb = __ballot_sync(0xffffffffu, m);
+        const int64_t mw = matched + __popc(mb & lt);
+        if (i < a && !m) {
+            const int64_t pos = i + bs - 2 * mw;
+            if (pos < cap) out[pos] = x; else over = true;
+        }
+        matched += __popc(mb);
+    }
+    int64_t matched2 = 0;
+    for (int base = 0; base < b; base += 32) {
+        const int k = base + lane;
+        const uint64_t y = k < b ? S[k] : EMPTY;
+        int64_t bw = 0;
+        bool m = false;
+        if (k < b) {
+            bw = lower_bound_u64(in, a, y);
+            m = bw < a && in[bw] == y;
+        }
+        const uint32_t mb = __ballot_sync(0xffffffffu, m);
+        const int64_t ms = matched2 + __popc(mb & lt);
+        if (k < b && !m) {
+            const int64_t pos = k + bw - 2 * ms;
+            if (pos < cap) out[pos] = y; else over = true;
+        }
+        matched2 += __popc(mb);
+    }
+    __syncwarp();
+    if (__any_sync(0xffffffffu, over)) return -1;
+    return a + b - 2 * matched;
+}
+
+// W <- W + D_x.  W lives in *W (size a) and the spare buffer *spare; the
+// pointers are swapped as pieces are merged.  Returns the new size or -1.
+template <int P>
+__device__ int64_t warp_add_coboundary(const Ctx& c, const Simplex<P>& x, uint64_t* stage, uint64_t*& W,
+                                       uint64_t*& spare, int64_t a, int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t n = c.R.n;
+    int64_t base = n - 1;
+    while (base >= 0) {
+        int fill = 0;
+        while (base >= 0 && fill <= STAGE - 32) {
+            const int64_t w = base - lane;
+            bool ok = w >= 0;
+#pragma unroll
+            for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
+            uint32_t rt = x.r;
+            if (ok) {
+#pragma unroll
+                for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
+                ok = rt <= c.thr;
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, ok);
+            if (ok) stage[fill + __popc(b & lt)] = row_key<P>(c, x, w, rt);
+            fill += __popc(b);
+            base -= 32;
+        }
+        int len = 32;
+        while (len < fill) len <<= 1;
+        for (int i = fill + lane; i < len; i += 32) stage[i] = EMPTY;
+        __syncwarp();
+        warp_bitonic(stage, len);
+        const int64_t na = warp_xor_merge(W, a, stage, fill, spare, cap);
+        __syncwarp();
+        if (na < 0) return -1;
+        uint64_t* t = W; W = spare; spare = t;
+        a = na;
+    }
+    return a;
+}
+
+// Owner of pivot row key rk among the columns before `self_key` in order:
+// returns true and fills `o`, or false if rk is no known pivot.
+template <int P>
+__device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex<P>& o) {
+    constexpr int NT = P + 2;
+    constexpr int NPAIR = NT * (NT - 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = c.R.n;
+    const uint32_t rt = (uint32_t)(rk >> c.rcb);
+    const uint64_t ct = c.rcmask - (rk & c.rcmask);
+    // 1. pivots of reduced columns: 32 probe slots at a time
+    {
+        uint64_t slot0 = mix64(ct) & c.hmask;
+        for (uint64_t probe = 0; probe <= c.hmask; probe += 32) {
+            const uint64_t sl = (slot0 + probe + lane) & c.hmask;
+            const uint64_t k = c.hkeys[sl];
+            const uint32_t hit = __ballot_sync(0xffffffffu, k == ct);
+            const uint32_t emp = __ballot_sync(0xffffffffu, k == EMPTY);
+            if (hit && (!emp || __ffs(hit) < __ffs(emp))) {
+                const uint32_t pos = __shfl_sync(0xffffffffu, c.hvals[sl], __ffs(hit) - 1);
+                const uint64_t okey = c.cols[pos];
+                if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL);
+                load_col<P>(c, okey, o);
+                return true;
+            }
+            if (emp) break;
+        }
+    }
+    // 2. apparent pairs (Def 5.3.4), recomputed
+    int tv[NT];
+    decode_simplex<P + 1>(c.B, ct, n - 1, tv);
+    bool eq = false;
+    int pi = 0, pj = 0;
+    if (lane < NPAIR) {
+        int k = lane;
+        pi = 1;
+        while (k >= pi) { k -= pi; ++pi; }
+        pj = k;
+        eq = c.R(tv[pi], tv[pj]) == rt;
+    }
+    int drop = -1;
+#pragma unroll
+    for (int m = NT - 1; m >= 0; --m) {  // largest vertex first = smallest facet index
+        if (drop < 0 && __ballot_sync(0xffffffffu, eq && pi != m && pj != m)) drop = m;
+    }
+    if (drop < 0) return false;
+    int k = 0;
+#pragma unroll
+    for (int q = 0; q < NT; ++q)
+        if (q != drop) o.v[k++] = tv[q];
+    const int64_t wd = tv[drop];
+    for (int64_t base = n - 1; base > wd; base -= 32) {
+        const int64_t w = base - lane;
+        bool ok = w > wd;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (w != o.v[q]);
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (c.R(o.v[q], w) <= rt);
+        if (__ballot_sync(0xffffffffu, ok)) return false;  // an older cofacet of s' exists
+    }
+    o.r = rt;
+    uint64_t cs = 0;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) cs += c.B(o.v[q], q + 1);
+    o.cidx = cs;
+    if (!(col_key<P>(c, o) < self_key)) atomicExch(c.err, DEV_INTERNAL);
+    return true;
+}
+
+// Reduce column j (position in cols) against the known pivots.
+template <int P>
+__device__ void reduce_one(const Ctx& c, int64_t j, int budget, uint64_t* stage, uint64_t* bufA, uint64_t* bufB,
+                           int64_t cap, uint64_t& out_key, uint8_t& out_status, uint32_t& out_adds) {
+    const uint64_t self_key = c.cols[j];
+    Simplex<P> s, o;
+    load_col<P>(c, self_key, s);
+    uint64_t piv = warp_column_pivot<P>(c, s);
+    out_adds = 0;
+    if (piv == EMPTY) { out_key = EMPTY; out_status = ST_COMPLETE; return; }
+    if (!warp_owner<P>(c, piv, self_key, o)) { out_key = piv; out_status = ST_COMPLETE; return; }
+    uint64_t* W = bufA;
+    uint64_t* spare = bufB;
+    int64_t a = warp_add_coboundary<P>(c, s, stage, W, spare, 0, cap);
+    if (a < 0) { out_key = piv; out_status = ST_OVERFLOW; return; }
+    uint32_t adds = 0;
+    for (;;) {
+        if ((int)adds >= budget) { out_key = piv; out_status = ST_BUDGET; out_adds = adds; return; }
+        const int64_t na = warp_add_coboundary<P>(c, o, stage, W, spare, a, cap);
+        if (na < 0) { out_key = piv; out_status = ST_OVERFLOW; out_adds = adds; return; }
+        ++adds;
+        a = na;
+        if (a == 0) { out_key = EMPTY; out_status = ST_COMPLETE; out_adds = adds; return; }
+        piv = W[0];
+        if (!warp_owner<P>(c, piv, self_key, o)) { out_key = piv; out_status = ST_COMPLETE; out_adds = adds; return; }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(RED_WARPS * 32)
+k_reduce_round(Ctx c, const uint32_t* __restrict__ U, int64_t u, int budget, uint64_t* __restrict__ cur_key,
+               uint8_t* __restrict__ status, uint32_t* __restrict__ adds, uint64_t* __restrict__ scratch,
+               int64_t cap, unsigned long long* __restrict__ work) {
+    __shared__ uint64_t stage_all[RED_WARPS][STAGE];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t slot = (int64_t)blockIdx.x * RED_WARPS + wid;
+    uint64_t* bufA = scratch + slot * 2 * cap;
+    uint64_t* bufB = bufA + cap;
+    for (;;) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(work, 1ull);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if ((int64_t)k >= u) break;
+        const int64_t j = U[k];
+        uint64_t key;
+        uint8_t st;
+        uint32_t ad;
+        reduce_one<P>(c, j, budget, stage_all[wid], bufA, bufB, cap, key, st, ad);
+        if (lane == 0) { cur_key[j] = key; status[j] = st; adds[j] = ad; }
+    }
+}
+
+__device__ void hash_insert(const Ctx& c, uint64_t key, uint32_t val) {
+    uint64_t sl = mix64(key) & c.hmask;
+    for (uint64_t probe = 0; probe <= c.hmask; ++probe) {
+        const unsigned long long prev =
+            atomicCAS(reinterpret_cast<unsigned long long*>(c.hkeys + sl), (unsigned long long)EMPTY,
+                      (unsigned long long)key);
+        if (prev == EMPTY || prev == key) { c.hvals[sl] = val; return; }
+        sl = (sl + 1) & c.hmask;
+    }
+    atomicExch(c.err, DEV_CAPACITY);
+}
+
+struct Emit {
+    PairRec* pairs;
+    unsigned long long* num_pairs;
+    uint32_t* clear_next;
+    unsigned long long* counters;  // [0] additions [1] pairs [2] essential
+    int keep_zero;
+};
+
+// Record the finished column j with pivot key `key` (EMPTY = zero column).
+__device__ void finish_column(const Ctx& c, const Emit& e, int64_t j, uint64_t key, uint32_t adds) {
+    const uint64_t ckey = c.cols[j];
+    const uint64_t cs = ckey & c.cmask;
+    const uint32_t rs = (uint32_t)((~(ckey >> c.cb)) & c.rmask);
+    PairRec pr;
+    pr.birth_rank = rs;
+    pr.birth_cidx = cs;
+    if (adds) atomicAdd(e.counters + 0, (unsigned long long)adds);
+    if (key == EMPTY) {  // zero column of an uncleared simplex: essential class
+        pr.death_rank = 0xFFFFFFFFu;
+        pr.death_cidx = -1;
+        atomicAdd(e.counters + 2, 1ull);
+        e.pairs[atomicAdd(e.num_pairs, 1ull)] = pr;
+        return;
+    }
+    const uint32_t rt = (uint32_t)(key >> c.rcb);
+    const uint64_t ct = c.rcmask - (key & c.rcmask);
+    hash_insert(c, ct, (uint32_t)j);
+    if (e.clear_next) atomicOr(e.clear_next + (ct >> 5), 1u << (ct & 31));
+    atomicAdd(e.counters + 1, 1ull);
+    if (rt > rs || e.keep_zero) {
+        pr.death_rank = rt;
+        pr.death_cidx = (int64_t)ct;
+        e.pairs[atomicAdd(e.num_pairs, 1ull)] = pr;
+    }
+}
+
+// One block: exclusive prefix-min of the pivot keys over U in order decides
+// which columns are final; the rest are compacted, in order, into Unext.
+__global__ void __launch_bounds__(1024)
+k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint64_t* __restrict__ cur_key,
+           const uint8_t* __restrict__ status, const uint32_t* __restrict__ adds, uint32_t* __restrict__ Unext,
+           unsigned long long* __restrict__ u_next) {
+    __shared__ uint64_t wmin[32];
+    __shared__ uint32_t wcnt[32];
+    __shared__ uint64_t carry_min;
+    __shared__ uint32_t carry_cnt;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) { carry_min = EMPTY; carry_cnt = 0; }
+    __syncthreads();
+    for (int64_t base = 0; base < u; base += blockDim.x) {
+        const int64_t k = base + threadIdx.x;
+        const bool valid = k < u;
+        const uint32_t j = valid ? U[k] : 0;
+        const uint64_t key = valid ? cur_key[j] : EMPTY;
+        const uint8_t st = valid ? status[j] : ST_COMPLETE;
+        // inclusive min-scan within the warp
+        uint64_t incl = key;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o && y < incl) incl = y;
+        }
+        if (lane == 31) wmin[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            uint64_t t = wmin[lane];
+            uint64_t ti = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint64_t y = __shfl_up_sync(0xffffffffu, ti, o);
+                if (lane >= o && y < ti) ti = y;
+            }
+            uint64_t ex = __shfl_up_sync(0xffffffffu, ti, 1);
+            wmin[lane] = lane == 0 ? EMPTY : ex;  // exclusive over warps
+        }
+        __syncthreads();
+        uint64_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) excl = EMPTY;
+        uint64_t pm = carry_min;
+        if (wmin[wid] < pm) pm = wmin[wid];
+        if (excl < pm) pm = excl;
+        const bool fin = valid && st == ST_COMPLETE && (key == EMPTY || key < pm);
+        if (fin) finish_column(c, e, j, key, adds[j]);
+        const bool keep = valid && !fin;
+        const uint32_t kb = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wcnt[wid] = __popc(kb);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < wid) before += wcnt[w];
+            total += wcnt[w];
+        }
+        if (keep) Unext[carry_cnt + before + __popc(kb & lt)] = j;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) {
+            uint64_t cm = carry_min;
+            if (wmin[wid] < cm) cm = wmin[wid];
+            if (incl < cm) cm = incl;
+            carry_min = cm;
+            carry_cnt += total;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *u_next = carry_cnt;
+}
+
+// One warp finishes the remaining columns in order (Algorithm 12 verbatim).
+template <int P>
+__global__ void __launch_bounds__(32)
+k_reduce_seq(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, uint64_t* bufA, uint64_t* bufB, int64_t cap) {
+    __shared__ uint64_t stage[STAGE];
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = 0; k < u; ++k) {
+        const int64_t j = U[k];
+        uint64_t key;
+        uint8_t st;
+        uint32_t ad;
+        reduce_one<P>(c, j, 0x7FFFFFFF, stage, bufA, bufB, cap, key, st, ad);
+        if (st != ST_COMPLETE) {
+            if (lane == 0) atomicExch(c.err, DEV_CAPACITY);
+            return;
+        }
+        if (lane == 0) finish_column(c, e, j, key, ad);
+        __threadfence_block();
+        __syncwarp();
+    }
+}
+
+__global__ void k_iota(uint32_t* U, int64_t m) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        U[k] = (uint32_t)k;
+}
+
+template <int P>
+void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
+    const int64_t m = c.num_cols;
+    cudaStream_t s = ws.stream;
+    uint32_t* U = ws.alloc_n<uint32_t>(m);
+    uint32_t* Un = ws.alloc_n<uint32_t>(m);
+    uint64_t* cur_key = ws.alloc_n<uint64_t>(m);
+    uint8_t* status = ws.alloc_n<uint8_t>(m);
+    uint32_t* adds = ws.alloc_n<uint32_t>(m);
+    unsigned long long* ctr = ws.zeros_n<unsigned long long>(2);  // [0] work, [1] u_next
+    k_iota<<<(unsigned)((m + 255) / 256 < 4096 ? (m + 255) / 256 : 4096), 256, 0, s>>>(U, m);
+    VR_CUDA(cudaGetLastError());
+    int64_t u = m;
+    const int SEQ_MIN = 32, MAX_ROUNDS = 64, BUDGET = 8;
+    const int64_t CAP_R = 8192;
+    const int64_t max_slots = 148 * 4 * RED_WARPS;
+    uint64_t* scratch = nullptr;
+    int64_t slots = 0;
+    for (int round = 0; round < MAX_ROUNDS && u > SEQ_MIN; ++round) {
+        int64_t want = u < max_slots ? u : max_slots;
+        want = (want + RED_WARPS - 1) / RED_WARPS * RED_WARPS;
+        if (want > slots) {
+            scratch = ws.alloc_n<uint64_t>((size_t)want * 2 * CAP_R);
+            slots = want;
+        }
+        VR_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s));
+        k_reduce_round<P><<<(unsigned)(want / RED_WARPS), RED_WARPS * 32, 0, s>>>(c, U, u, BUDGET, cur_key, status,
+                                                                                  adds, scratch, CAP_R, ctr);
+        k_finalize<<<1, 1024, 0, s>>>(c, e, U, u, cur_key, status, adds, Un, ctr + 1);
+        VR_CUDA(cudaGetLastError());
+        VR_CUDA(cudaMemcpyAsync(&hs.p[8], ctr + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaStreamSynchronize(s));
+        const int64_t un = hs.p[8];
+        uint32_t* t = U; U = Un; Un = t;
+        const bool stalled = un == u;
+        u = un;
+        if (stalled) break;
+    }
+    if (u > 0) {
+        const int64_t CAP_S = (int64_t)1 << 22;
+        uint64_t* big = ws.alloc_n<uint64_t>((size_t)2 * CAP_S);
+        k_reduce_seq<P><<<1, 32, 0, s>>>(c, e, U, u, big, big + CAP_S, CAP_S);
+        VR_CUDA(cudaGetLastError());
+    }
+}
+
+}  // namespace
+
+void run_reduction(const ReduceIn& in, const ReduceOut& out, bool keep_zero, Workspace& ws, HostScratch& hs) {
+    if (in.num_cols <= 0) return;
+    Ctx c;
+    c.R = in.R;
+    c.B = in.B;
+    c.thr = in.thr_rank;
+    c.cb = in.cidx_bits;
+    c.rcb = in.row_cidx_bits;
+    c.cmask = in.cidx_bits >= 64 ? ~0ull : ((1ull << in.cidx_bits) - 1);
+    c.rcmask = in.row_cidx_bits >= 64 ? ~0ull : ((1ull << in.row_cidx_bits) - 1);
+    c.rmask = in.rank_bits >= 64 ? ~0ull : ((1ull << in.rank_bits) - 1);
+    c.cols = in.cols;
+    c.num_cols = in.num_cols;
+    uint64_t hcap = 1024;
+    while (hcap < 2 * (uint64_t)in.num_cols) hcap <<= 1;
+    c.hkeys = ws.alloc_n<uint64_t>(hcap);
+    c.hvals = ws.alloc_n<uint32_t>(hcap);
+    VR_CUDA(cudaMemsetAsync(c.hkeys, 0xFF, hcap * sizeof(uint64_t), ws.stream));
+    c.hmask = hcap - 1;
+    c.err = out.dev_err;
+    Emit e;
+    e.pairs = out.pairs;
+    e.num_pairs = out.num_pairs;
+    e.clear_next = out.clear_next;
+    e.counters = out.counters;
+    e.keep_zero = keep_zero ? 1 : 0;
+    switch (in.p) {
+        case 1: run_p<1>(c, e, ws, hs); break;
+        case 2: run_p<2>(c, e, ws, hs); break;
+        case 3: run_p<3>(c, e, ws, hs); break;
+        case 4: run_p<4>(c, e, ws, hs); break;
+        case 5: run_p<5>(c, e, ws, hs); break;
+        case 6: run_p<6>(c, e, ws, hs); break;
+        default: throw Error{VR_ERR_INVALID_ARG};
+    }
+}
+
+}  // namespace vr

@@ -1,0 +1,206 @@
+// vr_common.cuh -- internal declarations shared by the libvrgpu translation
+// units (device helpers, the per-call workspace and the stage launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "vr.h"
+
+namespace vr {
+
+// ---------------------------------------------------------------------------
+// status plumbing
+// ---------------------------------------------------------------------------
+struct Error {
+    vr_status code;
+};
+
+#define VR_CUDA(expr)                                                        \
+    do {                                                                     \
+        cudaError_t e_ = (expr);                                             \
+        if (e_ != cudaSuccess) {                                             \
+            vr::set_last_cuda_error(e_, #expr, __FILE__, __LINE__);          \
+            throw vr::Error{e_ == cudaErrorMemoryAllocation ? VR_ERR_OOM     \
+                                                            : VR_ERR_CUDA}; \
+        }                                                                    \
+    } while (0)
+
+#define VR_CHECK(cond, status)                                               \
+    do {                                                                     \
+        if (!(cond)) throw vr::Error{status};                                \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Device-side error word written by kernels (bounded waits, capacity).
+enum DeviceError : int {
+    DEV_OK = 0,
+    DEV_CAPACITY = 1,   // a scratch buffer was too small
+    DEV_TIMEOUT = 2,    // a bounded wait ran out
+    DEV_INTERNAL = 3,   // a consistency check failed
+    DEV_BAD_INPUT = 4,  // NaN / negative distance
+};
+
+// ---------------------------------------------------------------------------
+// per-call workspace: stream-ordered allocations released together
+// ---------------------------------------------------------------------------
+class Workspace {
+  public:
+    explicit Workspace(cudaStream_t s);
+    ~Workspace();
+    void* alloc(size_t bytes);  // 256-byte aligned, not zeroed
+    template <class T>
+    T* alloc_n(size_t n) { return static_cast<T*>(alloc(n * sizeof(T) + 16)); }
+    template <class T>
+    T* zeros_n(size_t n) {
+        T* p = alloc_n<T>(n);
+        VR_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), stream));
+        return p;
+    }
+    void free_all();
+    cudaStream_t stream;
+
+  private:
+    std::vector<void*> ptrs_;
+};
+
+// Pinned host staging buffer for small device->host reads.
+struct HostScratch {
+    HostScratch();
+    ~HostScratch();
+    int64_t* p;  // 64 int64 slots
+};
+
+// ---------------------------------------------------------------------------
+// small helpers usable on host and device
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int bits_for(uint64_t maxval) {  // bits to hold 0..maxval
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+// Binomial table C(v, k) for v = 0..n, k = 0..K, layout [k][v] (row k is
+// contiguous in v), saturating at UINT64_MAX.
+struct Binom {
+    const uint64_t* t;  // device pointer, (K+1) * (n+1) entries
+    int64_t n;
+    int K;
+    __device__ __forceinline__ uint64_t operator()(int64_t v, int k) const {
+        return __ldg(t + (size_t)k * (size_t)(n + 1) + (size_t)v);
+    }
+};
+std::vector<uint64_t> host_binomials(int64_t n, int K);  // same layout on the host
+
+// Decode the q-simplex with index c (eq. 5.6) into ascending vertices v[0..q]:
+// v[q] is the largest v with C(v, q+1) <= c, then recurse on the remainder.
+template <int Q>
+__device__ __forceinline__ void decode_simplex(const Binom& B, uint64_t c, int64_t top, int* v) {
+#pragma unroll
+    for (int i = Q; i >= 0; --i) {
+        // largest x in [i, top] with C(x, i+1) <= c  (binary search)
+        int64_t lo = i, hi = top;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (B(mid, i + 1) <= c) lo = mid; else hi = mid - 1;
+        }
+        v[i] = (int)lo;
+        c -= B(lo, i + 1);
+        top = lo - 1;
+    }
+}
+
+// Diameter ranks: the distance matrix is replaced by the dense rank of each
+// entry among the distinct values {0} U {d(i,j)}, so that "diam(a) < diam(b)"
+// and "diam(a) == diam(b)" are integer comparisons; ranks map back to the
+// float values through a sorted table.  Row-major n x ld, symmetric.
+struct RankMatrix {
+    const uint32_t* r;
+    int64_t n;
+    int64_t ld;
+    __device__ __forceinline__ uint32_t operator()(int64_t i, int64_t j) const {
+        return __ldg(r + (size_t)i * (size_t)ld + (size_t)j);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// stage launchers (host side), one per translation unit
+// ---------------------------------------------------------------------------
+
+// dist.cu
+void launch_distances(const float* pts, int64_t n, int dim, float* lower_tri, cudaStream_t s);
+void launch_check_lower_tri(const float* lower_tri, int64_t m, int* dev_err, cudaStream_t s);
+
+// radix_sort.cu : LSD radix sort, ascending, stable, by the low `bits` bits.
+void radix_sort_u64(Workspace& ws, uint64_t* keys, uint64_t* vals, int64_t num, int bits);
+void radix_sort_u32(Workspace& ws, uint32_t* keys, uint32_t* vals, int64_t num, int bits);
+void scan_u32_exclusive(uint32_t* data, int64_t num, cudaStream_t s);  // in place, total < 2^32
+
+// rank.cu
+struct RankInfo {
+    uint32_t* rank;       // n x ld
+    int64_t ld;
+    float* values;        // device, distinct values ascending, values[0] == 0
+    int64_t num_values;   // host copy of the count
+    const int64_t* num_values_dev;
+    uint32_t enclosing_rank;  // rank of R = min_i max_j d(i,j)
+};
+RankInfo build_ranks(Workspace& ws, const float* lower_tri, int64_t n, HostScratch& hs);
+uint32_t threshold_rank(Workspace& ws, const RankInfo& ri, float threshold, HostScratch& hs);
+
+// Device-side records of emitted pairs (ranks, not values).
+struct PairRec {
+    uint32_t birth_rank;
+    uint32_t death_rank;  // UINT32_MAX for essential
+    uint64_t birth_cidx;
+    int64_t death_cidx;   // -1 for essential
+};
+
+// h0.cu : minimum spanning tree (Prim, strict order) + elder-rule pairing.
+// Writes n-1 finite pairs and the essential one to out (n records), sets the
+// dimension-1 clearing bits of the tree edges.
+void launch_h0(const RankMatrix& R, uint32_t thr_rank, PairRec* out, int* out_count,
+               uint32_t* clear_bits_dim1, int* dev_err, Workspace& ws);
+
+// apparent.cu : fused filtration construction with clearing (Alg 17/18)
+// and apparent-pair search (Lemma 5.3.6) for the p-simplices.
+struct ApparentOut {
+    uint64_t* nonapparent_keys;   // coboundary-order sort keys of non-apparent columns
+    unsigned long long* num_nonapparent;
+    uint32_t* clear_next;         // bitmap over (p+1)-simplices (NULL at the top dimension)
+    PairRec* zero_pairs;          // apparent pairs, only if keep_zero (else NULL)
+    unsigned long long* num_zero_pairs;
+    unsigned long long* counters; // [0] above_threshold [1] cleared [2] columns [3] apparent
+    int64_t capacity;             // capacity of nonapparent_keys
+    int* dev_err;
+};
+void launch_filtration_apparent(int p, const RankMatrix& R, const Binom& B, uint32_t thr_rank,
+                                const uint32_t* clear_bits, int cidx_bits, int rank_bits, uint64_t num_cand,
+                                const ApparentOut& o, cudaStream_t s);
+
+// reduce.cu : Z/2 reduction of the non-apparent columns (Algorithm 12).
+struct ReduceIn {
+    int p;
+    RankMatrix R;
+    Binom B;
+    uint32_t thr_rank;
+    int cidx_bits;        // bits of a p-simplex index in the column keys
+    int row_cidx_bits;    // bits of a (p+1)-simplex index in the row keys
+    int rank_bits;
+    const uint64_t* cols; // sorted column keys, num_cols
+    int64_t num_cols;
+};
+struct ReduceOut {
+    PairRec* pairs;               // capacity num_cols
+    unsigned long long* num_pairs;
+    uint32_t* clear_next;         // may be NULL
+    unsigned long long* counters; // [0] additions [1] pairs [2] essential
+    int* dev_err;
+};
+void run_reduction(const ReduceIn& in, const ReduceOut& out, bool keep_zero, Workspace& ws,
+                   HostScratch& hs);
+
+}  // namespace vr

@@ -1,0 +1,192 @@
+"""Python binding of libvrgpu (argument marshalling only).
+
+Every computation runs in the CUDA library behind the C ABI declared in
+``include/vr.h``; this module converts arrays and tensors to pointers and the
+returned ``vr_result`` into numpy arrays.  Importing it raises if the library
+has not been built (``python -m paper_2502_05063_b300.build``): there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvrgpu.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libvrgpu.so is not built; run `python -m paper_2502_05063_b300.build`")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+VR_MAX_DIM = 6
+VR_BATCH_MAX_N = 256
+VR_KEEP_ZERO_LENGTH = 0x1
+VR_CRITICAL_EDGES = 0x2
+
+STATUS = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_OOM", 3: "VR_ERR_INDEX_OVERFLOW",
+          4: "VR_ERR_CUDA", 5: "VR_ERR_TIMEOUT", 6: "VR_ERR_INTERNAL"}
+
+
+class VRError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+        super().__init__("%s failed: %s (%s)" % (where, self.name, lib.vr_status_string(code).decode()))
+
+
+class Pair(ctypes.Structure):
+    _fields_ = [("birth", ctypes.c_float), ("death", ctypes.c_float),
+                ("birth_simplex", ctypes.c_uint64), ("death_simplex", ctypes.c_int64)]
+
+
+STAT_FIELDS = ["candidates", "above_threshold", "cleared", "columns", "apparent", "reduced",
+               "additions", "pairs", "essential", "emitted"]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in STAT_FIELDS]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("dmax", ctypes.c_int32), ("n", ctypes.c_int64), ("threshold", ctypes.c_float),
+                ("count", ctypes.c_int64 * (VR_MAX_DIM + 1)),
+                ("pairs", ctypes.POINTER(Pair) * (VR_MAX_DIM + 1)),
+                ("critical_edges", ctypes.POINTER(ctypes.c_int32) * (VR_MAX_DIM + 1)),
+                ("stats", Stats * (VR_MAX_DIM + 1))]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("num_clouds", ctypes.c_int32), ("dmax", ctypes.c_int32),
+                ("pair_offsets", ctypes.POINTER(ctypes.c_int64) * 2),
+                ("pairs", ctypes.POINTER(Pair) * 2),
+                ("critical_edges", ctypes.POINTER(ctypes.c_int32) * 2),
+                ("thresholds", ctypes.POINTER(ctypes.c_float))]
+
+
+PAIR_DTYPE = np.dtype([("birth", "<f4"), ("death", "<f4"), ("birth_simplex", "<u8"), ("death_simplex", "<i8")])
+assert PAIR_DTYPE.itemsize == ctypes.sizeof(Pair)
+
+_vp, _i64, _i32, _u32, _f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_float
+lib.vr_status_string.restype = ctypes.c_char_p
+lib.vr_status_string.argtypes = [ctypes.c_int]
+lib.vr_barcodes_points.argtypes = [_vp, _i64, _i32, _i32, _f32, _u32, _vp, ctypes.POINTER(ctypes.POINTER(Result))]
+lib.vr_barcodes_dists.argtypes = [_vp, _i64, _i32, _f32, _u32, _vp, ctypes.POINTER(ctypes.POINTER(Result))]
+lib.vr_result_free.argtypes = [ctypes.POINTER(Result)]
+lib.vr_result_free.restype = None
+lib.vr_simplex_vertices.argtypes = [ctypes.c_uint64, _i32, _i64, _vp]
+lib.vr_distances.argtypes = [_vp, _i64, _i32, _vp, _vp]
+lib.vr_sort_u64.argtypes = [_vp, _vp, _i64, _i32, _vp]
+lib.vr_backward.argtypes = [_vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp]
+if hasattr(lib, "vr_barcodes_batched"):
+    lib.vr_barcodes_batched.argtypes = [_vp, _vp, _i32, _i32, _i32, _f32, _u32, _vp,
+                                        ctypes.POINTER(ctypes.POINTER(BatchResult))]
+    lib.vr_batch_result_free.argtypes = [ctypes.POINTER(BatchResult)]
+    lib.vr_batch_result_free.restype = None
+
+
+def _check(code, where):
+    if code != 0:
+        raise VRError(code, where)
+
+
+def _ptr_of(x):
+    """(pointer, keepalive) for a numpy array (host) or a torch tensor (host or CUDA)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), x
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Barcodes:
+    """Per-dimension pairs of one cloud.
+
+    pairs[p]          structured array (birth, death, birth_simplex, death_simplex)
+    critical_edges[p] int32 (m, 4) (u_b, v_b, u_d, v_d) if requested, else None
+    stats[p]          dict of the vr_stats counters
+    threshold         the threshold actually used
+    """
+
+    def __init__(self, res: Result):
+        self.dmax = res.dmax
+        self.n = res.n
+        self.threshold = res.threshold
+        self.pairs, self.critical_edges, self.stats = [], [], []
+        for p in range(res.dmax + 1):
+            m = res.count[p]
+            if m:
+                buf = ctypes.cast(res.pairs[p], ctypes.POINTER(ctypes.c_char * (m * PAIR_DTYPE.itemsize))).contents
+                self.pairs.append(np.frombuffer(bytes(buf), dtype=PAIR_DTYPE).copy())
+            else:
+                self.pairs.append(np.zeros(0, dtype=PAIR_DTYPE))
+            if res.critical_edges[p]:
+                e = np.ctypeslib.as_array(res.critical_edges[p], shape=(max(m, 1) * 4,))[: 4 * m]
+                self.critical_edges.append(e.reshape(m, 4).copy())
+            else:
+                self.critical_edges.append(None)
+            self.stats.append({f: getattr(res.stats[p], f) for f in STAT_FIELDS})
+
+
+def barcodes(points=None, dists=None, n=None, dmax=1, threshold=np.inf, flags=0, stream=None) -> Barcodes:
+    """Vietoris-Rips barcodes of a point cloud (float32 (n, D)) or of a
+    condensed lower-triangular distance vector (float32 n(n-1)/2), given as a
+    numpy array or a torch tensor on the host or the GPU."""
+    out = ctypes.POINTER(Result)()
+    if points is not None:
+        ptr, keep = _ptr_of(points)
+        nn, amb = int(points.shape[0]), int(points.shape[1])
+        code = lib.vr_barcodes_points(ptr, nn, amb, int(dmax), float(threshold), int(flags),
+                                      _stream_ptr(stream), ctypes.byref(out))
+    else:
+        ptr, keep = _ptr_of(dists)
+        if n is None:
+            m = int(dists.shape[0])
+            n = int(round((1 + (1 + 8 * m) ** 0.5) / 2))
+        code = lib.vr_barcodes_dists(ptr, int(n), int(dmax), float(threshold), int(flags),
+                                     _stream_ptr(stream), ctypes.byref(out))
+    _check(code, "vr_barcodes")
+    try:
+        return Barcodes(out.contents)
+    finally:
+        lib.vr_result_free(out)
+
+
+def simplex_vertices(cidx: int, q: int, n: int):
+    v = np.zeros(q + 1, dtype=np.int32)
+    _check(lib.vr_simplex_vertices(int(cidx), int(q), int(n), v.ctypes.data), "vr_simplex_vertices")
+    return [int(x) for x in v]
+
+
+def distances(pts_dev, out_dev, stream=None):
+    """Condensed distances of a CUDA float32 (n, D) tensor into a CUDA float32 tensor."""
+    _check(lib.vr_distances(pts_dev.data_ptr(), int(pts_dev.shape[0]), int(pts_dev.shape[1]),
+                            out_dev.data_ptr(), _stream_ptr(stream)), "vr_distances")
+
+
+def sort_u64(keys_dev, values_dev=None, bits=64, stream=None):
+    """In-place stable ascending radix sort of CUDA int64/uint64 tensors by the low `bits` bits."""
+    _check(lib.vr_sort_u64(keys_dev.data_ptr(), values_dev.data_ptr() if values_dev is not None else None,
+                           int(keys_dev.numel()), int(bits), _stream_ptr(stream)), "vr_sort_u64")
+
+
+def backward(pts_dev, edges_dev, grad_birth_dev, grad_death_dev, grad_pts_dev, stream=None):
+    _check(lib.vr_backward(pts_dev.data_ptr(), int(pts_dev.shape[0]), int(pts_dev.shape[1]), edges_dev.data_ptr(),
+                           int(edges_dev.shape[0]), grad_birth_dev.data_ptr(), grad_death_dev.data_ptr(),
+                           grad_pts_dev.data_ptr(), _stream_ptr(stream)), "vr_backward")
