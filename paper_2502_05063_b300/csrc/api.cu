@@ -16,6 +16,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "vr_common.cuh"
@@ -190,6 +191,40 @@ static HostPairs fetch_pairs(Workspace& ws, const PairRec* dev, int64_t num, int
 }
 
 // ---------------------------------------------------------------------------
+// optional stage log (VR_LOG=1): CUDA-event time of each stage on the stream
+// ---------------------------------------------------------------------------
+bool log_enabled() {
+    static const bool on = getenv("VR_LOG") && getenv("VR_LOG")[0] == '1';
+    return on;
+}
+
+struct StageLog {
+    bool on;
+    cudaStream_t s;
+    std::vector<std::pair<std::string, cudaEvent_t>> ev;
+    explicit StageLog(cudaStream_t st) : on(log_enabled()), s(st) { mark("start"); }
+    void mark(const std::string& name) {
+        if (!on) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        ev.emplace_back(name, e);
+    }
+    ~StageLog() {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        for (size_t i = 1; i < ev.size(); ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[i - 1].second, ev[i].second);
+            fprintf(stderr, "[vr] %-24s %9.3f ms\n", ev[i].first.c_str(), ms);
+        }
+        for (auto& e : ev) cudaEventDestroy(e.second);
+    }
+};
+
+static std::string stage_name(const char* what, int p) { return "dim" + std::to_string(p) + " " + what; }
+
+// ---------------------------------------------------------------------------
 // result assembly
 // ---------------------------------------------------------------------------
 static void fill_dim(vr_result* res, int p, const HostPairs& hp, const std::vector<float>& values, bool keep_zero,
@@ -251,7 +286,9 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         return res;
     }
     cudaStream_t s = ws.stream;
+    StageLog log(s);
     RankInfo ri = build_ranks(ws, lower, n, hs);
+    log.mark("ranks");
     const uint32_t thr = threshold_rank(ws, ri, threshold, hs);
     std::vector<float> values((size_t)ri.num_values);
     VR_CUDA(cudaMemcpyAsync(values.data(), ri.values, ri.num_values * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -275,6 +312,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
     PairRec* p0 = ws.alloc_n<PairRec>(n);
     int* p0n = ws.zeros_n<int>(1);
     launch_h0(R, thr, p0, p0n, clear, dev_err, ws);
+    log.mark("h0");
     VR_CUDA(cudaMemcpyAsync(&hs.p[0], p0n, sizeof(int), cudaMemcpyDeviceToHost, s));
     VR_CUDA(cudaStreamSynchronize(s));
     {
@@ -323,6 +361,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
             if (hs.p[4] <= cap) break;
             cap = hs.p[4];  // rerun with room for every non-apparent column
         }
+        log.mark(stage_name("apparent", p));
         check_dev_err(dev_err, s);
         vr_stats& st = res->stats[p];
         st.candidates = (int64_t)ncand;
@@ -334,6 +373,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         const int64_t nzero = hs.p[5];
         st.reduced = nna;
         radix_sort_u64(ws, keys, nullptr, nna, rank_bits + cb);
+        log.mark(stage_name("sort", p));
         PairRec* pr = ws.alloc_n<PairRec>(nna > 0 ? nna : 1);
         unsigned long long* rc = cnt + 8;  // [8] num_pairs [9] additions [10] pairs [11] essential
         ReduceIn in;
@@ -353,6 +393,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         out.counters = rc + 1;
         out.dev_err = dev_err;
         run_reduction(in, out, keep_zero, ws, hs);
+        log.mark(stage_name("reduce", p));
         VR_CUDA(cudaMemcpyAsync(hs.p + 8, rc, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         check_dev_err(dev_err, s);  // synchronises
         st.additions = hs.p[9];
@@ -365,6 +406,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
             hp.edges.insert(hp.edges.end(), hz.edges.begin(), hz.edges.end());
         }
         fill_dim(res, p, hp, values, keep_zero, want_edges);
+        log.mark(stage_name("emit", p));
         clear = clear_next;
     }
     guard.r = nullptr;

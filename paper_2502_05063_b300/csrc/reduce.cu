@@ -33,6 +33,10 @@
 // (drop the largest vertex whose removal keeps diam) has t as its oldest
 // cofacet (no larger added vertex keeps diam) -- Def 5.3.4 evaluated on the
 // fly in one warp.  No wait in this file spins on another thread.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
 #include "vr_common.cuh"
 
 namespace vr {
@@ -56,6 +60,13 @@ struct Ctx {
     uint32_t* hvals;   // column position
     uint64_t hmask;
     int* err;
+    // finished columns that needed additions keep their reduced form R_j here,
+    // so a later column adds R_j (standard reduction) instead of D_j
+    uint64_t* pool;
+    unsigned long long* pool_used;
+    int64_t pool_cap;
+    uint64_t* rc_off;  // per column position
+    uint32_t* rc_len;  // 0: the column is its own coboundary D_j
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -161,7 +172,7 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t le
 
 // out = in XOR S (symmetric difference of two sorted sets), returns the new
 // size or -1 if it would exceed cap.
-__device__ int64_t warp_xor_merge(const uint64_t* in, int64_t a, const uint64_t* S, int b, uint64_t* out,
+__device__ int64_t warp_xor_merge(const uint64_t* in, int64_t a, const uint64_t* S, int64_t b, uint64_t* out,
                                   int64_t cap) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -185,8 +196,8 @@ __device__ int64_t warp_xor_merge(const uint64_t* in, int64_t a, const uint64_t*
         matched += __popc(mb);
     }
     int64_t matched2 = 0;
-    for (int base = 0; base < b; base += 32) {
-        const int k = base + lane;
+    for (int64_t base = 0; base < b; base += 32) {
+        const int64_t k = base + lane;
         const uint64_t y = k < b ? S[k] : EMPTY;
         int64_t bw = 0;
         bool m = false;
@@ -248,32 +259,42 @@ __device__ int64_t warp_add_coboundary(const Ctx& c, const Simplex<P>& x, uint64
     return a;
 }
 
+// Position of the finished column whose pivot is the (p+1)-simplex ct, or -1;
+// one warp probes 32 slots of the open-addressing table at a time.
+__device__ int64_t warp_hash_find(const Ctx& c, uint64_t ct) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t slot0 = mix64(ct) & c.hmask;
+    for (uint64_t probe = 0; probe <= c.hmask; probe += 32) {
+        const uint64_t sl = (slot0 + probe + lane) & c.hmask;
+        const uint64_t k = c.hkeys[sl];
+        const uint32_t hit = __ballot_sync(0xffffffffu, k == ct);
+        const uint32_t emp = __ballot_sync(0xffffffffu, k == EMPTY);
+        if (hit && (!emp || __ffs(hit) < __ffs(emp)))
+            return (int64_t)__shfl_sync(0xffffffffu, c.hvals[sl], __ffs(hit) - 1);
+        if (emp) break;
+    }
+    return -1;
+}
+
 // Owner of pivot row key rk among the columns before `self_key` in order:
 // returns true and fills `o`, or false if rk is no known pivot.
 template <int P>
-__device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex<P>& o) {
+__device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex<P>& o, int64_t& opos) {
     constexpr int NT = P + 2;
     constexpr int NPAIR = NT * (NT - 1) / 2;
     const int lane = threadIdx.x & 31;
     const int64_t n = c.R.n;
     const uint32_t rt = (uint32_t)(rk >> c.rcb);
     const uint64_t ct = c.rcmask - (rk & c.rcmask);
-    // 1. pivots of reduced columns: 32 probe slots at a time
+    // 1. pivots of reduced columns
     {
-        uint64_t slot0 = mix64(ct) & c.hmask;
-        for (uint64_t probe = 0; probe <= c.hmask; probe += 32) {
-            const uint64_t sl = (slot0 + probe + lane) & c.hmask;
-            const uint64_t k = c.hkeys[sl];
-            const uint32_t hit = __ballot_sync(0xffffffffu, k == ct);
-            const uint32_t emp = __ballot_sync(0xffffffffu, k == EMPTY);
-            if (hit && (!emp || __ffs(hit) < __ffs(emp))) {
-                const uint32_t pos = __shfl_sync(0xffffffffu, c.hvals[sl], __ffs(hit) - 1);
-                const uint64_t okey = c.cols[pos];
-                if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL);
-                load_col<P>(c, okey, o);
-                return true;
-            }
-            if (emp) break;
+        const int64_t pos = warp_hash_find(c, ct);
+        if (pos >= 0) {
+            const uint64_t okey = c.cols[pos];
+            if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL);
+            load_col<P>(c, okey, o);
+            opos = pos;
+            return true;
         }
     }
     // 2. apparent pairs (Def 5.3.4), recomputed
@@ -314,20 +335,59 @@ __device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex
     for (int q = 0; q <= P; ++q) cs += c.B(o.v[q], q + 1);
     o.cidx = cs;
     if (!(col_key<P>(c, o) < self_key)) atomicExch(c.err, DEV_INTERNAL);
+    opos = -1;
     return true;
 }
 
-// Reduce column j (position in cols) against the known pivots.
+// W <- W + R_o: the stored reduced column of a finished column, or its
+// coboundary when none is stored (apparent columns, zero-addition columns).
+template <int P>
+__device__ int64_t warp_add_owner(const Ctx& c, const Simplex<P>& o, int64_t opos, uint64_t* stage, uint64_t*& W,
+                                  uint64_t*& spare, int64_t a, int64_t cap) {
+    if (opos >= 0) {
+        const uint32_t len = c.rc_len[opos];
+        if (len) {
+            const int64_t na = warp_xor_merge(W, a, c.pool + c.rc_off[opos], len, spare, cap);
+            __syncwarp();
+            if (na < 0) return -1;
+            uint64_t* t = W; W = spare; spare = t;
+            return na;
+        }
+    }
+    return warp_add_coboundary<P>(c, o, stage, W, spare, a, cap);
+}
+
+// Keep the reduced column of position j (W[0..a)) for later additions.
+__device__ void store_reduced(const Ctx& c, int64_t j, const uint64_t* W, int64_t a) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(c.pool_used, (unsigned long long)a);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    const bool fits = (int64_t)(off + a) <= c.pool_cap && a <= 0xFFFFFFFFll;
+    if (fits)
+        for (int64_t i = lane; i < a; i += 32) c.pool[off + i] = W[i];
+    __syncwarp();
+    if (lane == 0) {
+        c.rc_off[j] = off;
+        c.rc_len[j] = fits ? (uint32_t)a : 0u;  // no room: later additions regenerate D_j
+    }
+}
+
+// Reduce column j (position in cols) against the known pivots.  At most
+// `budget` additions; on completion with additions the result is stored.
 template <int P>
 __device__ void reduce_one(const Ctx& c, int64_t j, int budget, uint64_t* stage, uint64_t* bufA, uint64_t* bufB,
                            int64_t cap, uint64_t& out_key, uint8_t& out_status, uint32_t& out_adds) {
+    const int lane = threadIdx.x & 31;
     const uint64_t self_key = c.cols[j];
     Simplex<P> s, o;
+    int64_t opos = -1;
     load_col<P>(c, self_key, s);
     uint64_t piv = warp_column_pivot<P>(c, s);
     out_adds = 0;
+    if (lane == 0) c.rc_len[j] = 0;
     if (piv == EMPTY) { out_key = EMPTY; out_status = ST_COMPLETE; return; }
-    if (!warp_owner<P>(c, piv, self_key, o)) { out_key = piv; out_status = ST_COMPLETE; return; }
+    if (!warp_owner<P>(c, piv, self_key, o, opos)) { out_key = piv; out_status = ST_COMPLETE; return; }
     uint64_t* W = bufA;
     uint64_t* spare = bufB;
     int64_t a = warp_add_coboundary<P>(c, s, stage, W, spare, 0, cap);
@@ -335,13 +395,19 @@ __device__ void reduce_one(const Ctx& c, int64_t j, int budget, uint64_t* stage,
     uint32_t adds = 0;
     for (;;) {
         if ((int)adds >= budget) { out_key = piv; out_status = ST_BUDGET; out_adds = adds; return; }
-        const int64_t na = warp_add_coboundary<P>(c, o, stage, W, spare, a, cap);
+        const int64_t na = warp_add_owner<P>(c, o, opos, stage, W, spare, a, cap);
         if (na < 0) { out_key = piv; out_status = ST_OVERFLOW; out_adds = adds; return; }
         ++adds;
         a = na;
         if (a == 0) { out_key = EMPTY; out_status = ST_COMPLETE; out_adds = adds; return; }
         piv = W[0];
-        if (!warp_owner<P>(c, piv, self_key, o)) { out_key = piv; out_status = ST_COMPLETE; out_adds = adds; return; }
+        if (!warp_owner<P>(c, piv, self_key, o, opos)) {
+            out_key = piv;
+            out_status = ST_COMPLETE;
+            out_adds = adds;
+            store_reduced(c, j, W, a);
+            return;
+        }
     }
 }
 
@@ -422,7 +488,7 @@ __device__ void finish_column(const Ctx& c, const Emit& e, int64_t j, uint64_t k
 __global__ void __launch_bounds__(1024)
 k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint64_t* __restrict__ cur_key,
            const uint8_t* __restrict__ status, const uint32_t* __restrict__ adds, uint32_t* __restrict__ Unext,
-           unsigned long long* __restrict__ u_next) {
+           unsigned long long* __restrict__ u_next, unsigned long long* __restrict__ first_status) {
     __shared__ uint64_t wmin[32];
     __shared__ uint32_t wcnt[32];
     __shared__ uint64_t carry_min;
@@ -464,6 +530,7 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
         if (wmin[wid] < pm) pm = wmin[wid];
         if (excl < pm) pm = excl;
         const bool fin = valid && st == ST_COMPLETE && (key == EMPTY || key < pm);
+        if (k == 0) *first_status = st;
         if (fin) finish_column(c, e, j, key, adds[j]);
         const bool keep = valid && !fin;
         const uint32_t kb = __ballot_sync(0xffffffffu, keep);
@@ -486,6 +553,466 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
         __syncthreads();
     }
     if (threadIdx.x == 0) *u_next = carry_cnt;
+}
+
+// ---------------------------------------------------------------------------
+// Heavy columns: one 512-thread block per column, state kept across rounds.
+//
+// A column that needs many additions (the cocycle of a long bar can reach
+// hundreds of thousands of rows) is never merged as a whole.  Its rows are
+// split at a key Ks: the front F (rows < Ks, sorted, unique, at most FC of
+// them) lives in shared memory and is the only part the pivot search reads;
+// the back B (rows >= Ks) is an unsorted multiset in global memory to which
+// new rows are appended without sorting.  When F runs empty, a most-
+// significant-digit radix select over B finds a split T with at most FC/2
+// rows below it; those rows are sorted, rows of even multiplicity cancel
+// (Z/2), and the rest become the new front with Ks = T.  An addition thus
+// costs O(rows added + |F|), independent of the column's size.
+// ---------------------------------------------------------------------------
+constexpr int HT = 512;          // threads per block
+constexpr int HW = HT / 32;
+constexpr int FC = 8192;         // front capacity
+constexpr int FKEEP = FC - 2048; // front size kept after a spill
+constexpr int HSTAGE = 1024;     // rows generated or copied per pass (power of two >= HT)
+
+struct HeavyState {
+    uint64_t* F;       // slots x FC, the front saved between rounds
+    uint64_t* B;       // slots x bcap
+    int64_t bcap;
+    uint64_t* Ks;      // per slot
+    int32_t* fsize;
+    int64_t* bsize;
+    uint8_t* init;     // 0: the column has not been started (or must restart)
+    uint32_t* adds;
+};
+
+struct HeavySmem {
+    uint64_t F[FC];
+    uint64_t F2[2 * FC];
+    uint64_t stage[HSTAGE];
+    int ws[HW + 1];
+    uint32_t hist[256];
+    uint64_t Ks;
+    int64_t bsize;
+    int64_t opos;
+    int fsize;
+    int flag;
+    int ov[VR_MAX_DIM + 2];
+    uint32_t orank;
+    uint64_t sel;     // radix-select result
+};
+
+// exclusive block scan of one int per thread; *total receives the sum
+__device__ __forceinline__ int block_excl_scan(int x, int* ws, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < HW ? ws[lane] : 0;
+        int ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < HW) ws[lane] = ti - t;
+        if (lane == HW - 1) ws[HW] = ti;
+    }
+    __syncthreads();
+    const int r = ws[wid] + incl - x;
+    *total = ws[HW];
+    __syncthreads();
+    return r;
+}
+
+__device__ void block_bitonic(uint64_t* a, int len) {
+    for (int k = 2; k <= len; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < len; i += HT) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t x = a[i], y = a[ixj];
+                    if ((x > y) == ((i & k) == 0)) { a[i] = y; a[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__device__ __forceinline__ int lower_bound_sm(const uint64_t* a, int len, uint64_t x) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Append rows to B; false (and nothing written) if B is full.
+__device__ bool heavy_append(HeavySmem& S, uint64_t* B, int64_t bcap, const uint64_t* src, int cnt) {
+    const int64_t bs = S.bsize;
+    if (bs + cnt > bcap) return false;
+    for (int i = threadIdx.x; i < cnt; i += HT) B[bs + i] = src[i];
+    __syncthreads();
+    if (threadIdx.x == 0) S.bsize = bs + cnt;
+    __syncthreads();
+    return true;
+}
+
+// W <- W + run, run = S.stage[0..b) sorted and unique.  False on B overflow.
+__device__ bool heavy_add_run(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
+    const uint64_t* run = S.stage;
+    const uint64_t Ks = S.Ks;
+    const int lo = lower_bound_sm(run, b, Ks);  // run[0..lo) < Ks <= run[lo..b)
+    if (!heavy_append(S, B, bcap, run + lo, b - lo)) return false;
+    const int a = S.fsize;
+    // front rows: matches against run[0..lo) decide their position in F2
+    const int chunkF = (a + HT - 1) / HT;
+    const int f0 = min(a, (int)threadIdx.x * chunkF), f1 = min(a, f0 + chunkF);
+    int mloc = 0;
+    for (int i = f0; i < f1; ++i) {
+        int p = lower_bound_sm(run, lo, S.F[i]);
+        mloc += (p < lo && run[p] == S.F[i]);
+    }
+    int mtot;
+    int m = block_excl_scan(mloc, S.ws, &mtot);
+    for (int i = f0; i < f1; ++i) {
+        const uint64_t x = S.F[i];
+        const int p = lower_bound_sm(run, lo, x);
+        if (p < lo && run[p] == x) { ++m; continue; }
+        S.F2[i + p - 2 * m] = x;
+    }
+    const int chunkR = (lo + HT - 1) / HT;
+    const int r0 = min(lo, (int)threadIdx.x * chunkR), r1 = min(lo, r0 + chunkR);
+    int mloc2 = 0;
+    for (int k = r0; k < r1; ++k) {
+        int p = lower_bound_sm(S.F, a, run[k]);
+        mloc2 += (p < a && S.F[p] == run[k]);
+    }
+    int mt2;
+    int m2 = block_excl_scan(mloc2, S.ws, &mt2);
+    for (int k = r0; k < r1; ++k) {
+        const uint64_t y = run[k];
+        const int p = lower_bound_sm(S.F, a, y);
+        if (p < a && S.F[p] == y) { ++m2; continue; }
+        S.F2[k + p - 2 * m2] = y;
+    }
+    __syncthreads();
+    int na = a + lo - 2 * mtot;
+    if (na > FKEEP) {  // spill the top of the front to B and lower the split
+        if (!heavy_append(S, B, bcap, S.F2 + FKEEP, na - FKEEP)) return false;
+        if (threadIdx.x == 0) S.Ks = S.F2[FKEEP];
+        na = FKEEP;
+    }
+    for (int i = threadIdx.x; i < na; i += HT) S.F[i] = S.F2[i];
+    if (threadIdx.x == 0) S.fsize = na;
+    __syncthreads();
+    return true;
+}
+
+// Refill an empty front from B.  Returns false if the column is zero.
+__device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
+    const int target = FC / 2;
+    for (;;) {
+        __syncthreads();
+        const int64_t bsz = S.bsize;
+        if (bsz == 0) return false;
+        // 1. split T with at most `target` rows below it
+        if (threadIdx.x == 0) S.flag = 0;
+        uint64_t T = EMPTY;
+        if (bsz > target) {
+            uint64_t prefix = 0;
+            int shift = ((keybits + 7) / 8) * 8 - 8;
+            if (shift < 0) shift = 0;
+            int64_t below = 0;
+            for (;;) {
+                for (int i = threadIdx.x; i < 256; i += HT) S.hist[i] = 0;
+                __syncthreads();
+                for (int64_t i = threadIdx.x; i < bsz; i += HT) {
+                    const uint64_t k = B[i];
+                    const bool in = shift + 8 >= 64 || (k >> (shift + 8)) == (prefix >> (shift + 8));
+                    if (in) atomicAdd(&S.hist[(k >> shift) & 0xFF], 1u);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int d = 0;
+                    int64_t bl = below;
+                    while (d < 256 && bl + S.hist[d] <= target) bl += S.hist[d++];
+                    const uint64_t binstart = (prefix & ~((shift + 8 >= 64) ? ~0ull : ((1ull << (shift + 8)) - 1))) |
+                                              ((uint64_t)d << shift);
+                    if (bl > 0) { S.sel = binstart; S.flag = 1; }          // rows below the bin fit
+                    else if (shift == 0) { S.sel = binstart; S.flag = 2; }  // one key, many copies
+                    else { S.sel = binstart; S.flag = 0; }                  // descend into bin d
+                    S.ws[HW] = (int)bl;
+                }
+                __syncthreads();
+                const int fl = S.flag;
+                if (fl == 1) { T = S.sel; break; }
+                if (fl == 2) { T = S.sel + 1; break; }
+                prefix = S.sel;
+                below = S.ws[HW];
+                shift -= 8;
+                __syncthreads();
+            }
+        }
+        // 2. move rows < T to F2 (tile by tile, so in-place compaction of B is safe)
+        int nlt = 0;
+        int64_t nge = 0;
+        for (int64_t base = 0; base < bsz; base += HT) {
+            const int64_t i = base + threadIdx.x;
+            const uint64_t k = i < bsz ? B[i] : EMPTY;
+            const bool lt = i < bsz && k < T;
+            const bool ge = i < bsz && !lt;
+            int tl, tg;
+            const int pl = block_excl_scan(lt, S.ws, &tl);
+            const int pg = block_excl_scan(ge, S.ws, &tg);  // syncs: all of this tile was read
+            if (lt && nlt + pl < 2 * FC) S.F2[nlt + pl] = k;
+            if (ge) B[nge + pg] = k;
+            nlt += tl;
+            nge += tg;
+        }
+        __syncthreads();
+        if (nlt > 2 * FC) {  // a single key with more copies than fit: keep its parity only
+            if (threadIdx.x == 0) {
+                S.F[0] = T - 1;
+                S.fsize = (nlt & 1) ? 1 : 0;
+                S.bsize = nge;
+                S.Ks = T;
+            }
+            __syncthreads();
+            if (S.fsize) return true;
+            continue;
+        }
+        int len = 1;
+        while (len < nlt) len <<= 1;
+        for (int i = nlt + threadIdx.x; i < len; i += HT) S.F2[i] = EMPTY;
+        __syncthreads();
+        block_bitonic(S.F2, len);
+        // 3. keep the rows of odd multiplicity
+        const int chunk = (nlt + HT - 1) / HT;
+        const int c0 = min(nlt, (int)threadIdx.x * chunk), c1 = min(nlt, c0 + chunk);
+        int keep = 0;
+        for (int i = c0; i < c1; ++i) {
+            if (i > 0 && S.F2[i - 1] == S.F2[i]) continue;
+            int e = i;
+            while (e + 1 < nlt && S.F2[e + 1] == S.F2[i]) ++e;
+            keep += ((e - i + 1) & 1);
+        }
+        int tk;
+        int pos = block_excl_scan(keep, S.ws, &tk);
+        for (int i = c0; i < c1; ++i) {
+            if (i > 0 && S.F2[i - 1] == S.F2[i]) continue;
+            int e = i;
+            while (e + 1 < nlt && S.F2[e + 1] == S.F2[i]) ++e;
+            if ((e - i + 1) & 1) S.F[pos++] = S.F2[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S.fsize = tk;
+            S.bsize = nge;
+            S.Ks = T;
+        }
+        __syncthreads();
+        if (tk > 0) return true;
+    }
+}
+
+// W <- W + D_x for the p-simplex x (vertices ascending, diameter rank xr).
+template <int P>
+__device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x) {
+    const int64_t n = c.R.n;
+    for (int64_t base = n - 1; base >= 0; base -= HT) {
+        const int64_t w = base - (int64_t)threadIdx.x;
+        bool ok = w >= 0;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
+        uint32_t rt = x.r;
+        if (ok) {
+#pragma unroll
+            for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
+            ok = rt <= c.thr;
+        }
+        int tot;
+        const int pos = block_excl_scan(ok, S.ws, &tot);
+        if (ok) S.stage[pos] = row_key<P>(c, x, w, rt);
+        int len = 2;
+        while (len < tot) len <<= 1;
+        for (int i = tot + threadIdx.x; i < len; i += HT) S.stage[i] = EMPTY;
+        __syncthreads();
+        block_bitonic(S.stage, len);
+        if (!heavy_add_run(S, B, bcap, tot)) return false;
+    }
+    return true;
+}
+
+// W <- W + R_o where R_o is a stored reduced column (sorted, unique).
+__device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, int64_t opos) {
+    const uint64_t* run = c.pool + c.rc_off[opos];
+    const int64_t len = c.rc_len[opos];
+    for (int64_t base = 0; base < len; base += HSTAGE) {
+        const int cnt = (int)min((int64_t)HSTAGE, len - base);
+        for (int i = threadIdx.x; i < cnt; i += HT) S.stage[i] = run[base + i];
+        __syncthreads();
+        if (!heavy_add_run(S, B, bcap, cnt)) return false;
+    }
+    return true;
+}
+
+// Owner of pivot rk (see warp_owner); result in S.opos / S.ov / S.orank.
+template <int P>
+__device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t self_key) {
+    constexpr int NT = P + 2;
+    constexpr int NPAIR = NT * (NT - 1) / 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n = c.R.n;
+    const uint32_t rt = (uint32_t)(rk >> c.rcb);
+    const uint64_t ct = c.rcmask - (rk & c.rcmask);
+    if (wid == 0) {
+        int64_t pos = warp_hash_find(c, ct);
+        int flag = 0;  // 1 = stored column owner, 2 = candidate apparent owner, 0 = none
+        int drop = -1;
+        int tv[NT];
+        if (pos >= 0) {
+            flag = 1;
+        } else {
+            decode_simplex<P + 1>(c.B, ct, n - 1, tv);
+            bool eq = false;
+            int pi = 0, pj = 0;
+            if (lane < NPAIR) {
+                int k = lane;
+                pi = 1;
+                while (k >= pi) { k -= pi; ++pi; }
+                pj = k;
+                eq = c.R(tv[pi], tv[pj]) == rt;
+            }
+#pragma unroll
+            for (int m = NT - 1; m >= 0; --m)
+                if (drop < 0 && __ballot_sync(0xffffffffu, eq && pi != m && pj != m)) drop = m;
+            if (drop >= 0) flag = 2;
+        }
+        if (lane == 0) {
+            S.flag = flag;
+            S.opos = pos;
+            if (flag == 2) {
+                int k = 0;
+                for (int q = 0; q < NT; ++q)
+                    if (q != drop) S.ov[k++] = tv[q];
+                S.ov[P + 1] = tv[drop];  // the dropped vertex
+                S.orank = rt;
+            }
+        }
+    }
+    __syncthreads();
+    const int flag = S.flag;
+    if (flag == 0) return false;
+    if (flag == 1) {
+        if (threadIdx.x == 0) {
+            const uint64_t okey = c.cols[S.opos];
+            if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL);
+        }
+        return true;
+    }
+    // apparent iff no vertex w above the dropped one keeps the diameter of s'
+    int ov[P + 1];
+#pragma unroll
+    for (int q = 0; q <= P; ++q) ov[q] = S.ov[q];
+    const int64_t wd = S.ov[P + 1];
+    bool older = false;
+    for (int64_t base = n - 1; base > wd; base -= HT) {
+        const int64_t w = base - (int64_t)threadIdx.x;
+        bool ok = w > wd;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (w != ov[q]);
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (c.R(ov[q], w) <= rt);
+        older = older || ok;
+    }
+    return !__syncthreads_or(older);
+}
+
+template <int P>
+__global__ void __launch_bounds__(HT)
+k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t* __restrict__ slot_of,
+               HeavyState hs, int budget, int keybits, uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status,
+               uint32_t* __restrict__ adds_out) {
+    extern __shared__ __align__(16) unsigned char hsm[];
+    HeavySmem& S = *reinterpret_cast<HeavySmem*>(hsm);
+    const int64_t k = blockIdx.x;
+    if (k >= u) return;
+    const int64_t j = U[k];
+    const int64_t slot = slot_of[j];
+    uint64_t* B = hs.B + slot * hs.bcap;
+    const uint64_t self_key = c.cols[j];
+    Simplex<P> s;
+    load_col<P>(c, self_key, s);
+    uint32_t adds;
+    bool ok = true;
+    if (!hs.init[slot]) {
+        if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.Ks = EMPTY; }
+        __syncthreads();
+        adds = 0;
+        ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, s);
+    } else {
+        if (threadIdx.x == 0) { S.fsize = hs.fsize[slot]; S.bsize = hs.bsize[slot]; S.Ks = hs.Ks[slot]; }
+        adds = hs.adds[slot];
+        __syncthreads();
+        for (int i = threadIdx.x; i < S.fsize; i += HT) S.F[i] = hs.F[slot * FC + i];
+        __syncthreads();
+    }
+    uint64_t key = ok ? EMPTY : 0;  // 0: no consistent state yet, the smallest (always valid) bound
+    uint8_t st = ST_COMPLETE;
+    int done = 0;
+    while (ok) {
+        if (S.fsize == 0 && !heavy_refill(S, B, keybits)) { key = EMPTY; break; }  // zero column
+        key = S.F[0];
+        if (!heavy_owner<P>(c, S, key, self_key)) break;  // pivot unknown: complete
+        if (done >= budget) { st = ST_BUDGET; break; }
+        if (S.flag == 1) {
+            const int64_t opos = S.opos;
+            if (c.rc_len[opos]) {
+                ok = heavy_add_stored(c, S, B, hs.bcap, opos);
+            } else {
+                Simplex<P> o;
+                load_col<P>(c, c.cols[opos], o);
+                ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, o);
+            }
+        } else {
+            Simplex<P> o;
+#pragma unroll
+            for (int q = 0; q <= P; ++q) o.v[q] = S.ov[q];
+            o.r = S.orank;
+            ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, o);
+        }
+        ++adds;
+        ++done;
+        __syncthreads();
+    }
+    if (!ok) st = ST_OVERFLOW;  // key holds the last consistent pivot, a valid bound
+    for (int i = threadIdx.x; i < S.fsize && ok; i += HT) hs.F[slot * FC + i] = S.F[i];
+    if (threadIdx.x == 0) {
+        hs.fsize[slot] = S.fsize;
+        hs.bsize[slot] = S.bsize;
+        hs.Ks[slot] = S.Ks;
+        hs.adds[slot] = adds;
+        hs.init[slot] = ok ? 1 : 0;  // an overflowed column restarts from scratch
+        cur_key[j] = key;
+        status[j] = st;
+        adds_out[j] = adds;
+    }
+}
+
+__global__ void k_assign_slots(const uint32_t* __restrict__ U, int64_t u, uint32_t* __restrict__ slot_of,
+                               uint8_t* __restrict__ init) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x) {
+        slot_of[U[k]] = (uint32_t)k;
+        init[k] = 0;
+    }
 }
 
 // One warp finishes the remaining columns in order (Algorithm 12 verbatim).
@@ -524,40 +1051,83 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
     uint64_t* cur_key = ws.alloc_n<uint64_t>(m);
     uint8_t* status = ws.alloc_n<uint8_t>(m);
     uint32_t* adds = ws.alloc_n<uint32_t>(m);
-    unsigned long long* ctr = ws.zeros_n<unsigned long long>(2);  // [0] work, [1] u_next
+    unsigned long long* ctr = ws.zeros_n<unsigned long long>(3);  // [0] work [1] u_next [2] first status
     k_iota<<<(unsigned)((m + 255) / 256 < 4096 ? (m + 255) / 256 : 4096), 256, 0, s>>>(U, m);
     VR_CUDA(cudaGetLastError());
     int64_t u = m;
-    const int SEQ_MIN = 32, MAX_ROUNDS = 64, BUDGET = 8;
-    const int64_t CAP_R = 8192;
-    const int64_t max_slots = 148 * 4 * RED_WARPS;
-    uint64_t* scratch = nullptr;
-    int64_t slots = 0;
-    for (int round = 0; round < MAX_ROUNDS && u > SEQ_MIN; ++round) {
-        int64_t want = u < max_slots ? u : max_slots;
-        want = (want + RED_WARPS - 1) / RED_WARPS * RED_WARPS;
-        if (want > slots) {
-            scratch = ws.alloc_n<uint64_t>((size_t)want * 2 * CAP_R);
-            slots = want;
-        }
+    const int keybits = bits_for(c.rmask) + c.rcb;
+    // Phase 1: one warp per column, at most 8 additions, every column at once.
+    {
+        const int64_t max_slots = 148 * 4 * RED_WARPS;
+        int64_t slots = u < max_slots ? u : max_slots;
+        slots = (slots + RED_WARPS - 1) / RED_WARPS * RED_WARPS;
+        const int64_t cap = 8192;
+        uint64_t* scratch = ws.alloc_n<uint64_t>((size_t)slots * 2 * cap);
         VR_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s));
-        k_reduce_round<P><<<(unsigned)(want / RED_WARPS), RED_WARPS * 32, 0, s>>>(c, U, u, BUDGET, cur_key, status,
-                                                                                  adds, scratch, CAP_R, ctr);
-        k_finalize<<<1, 1024, 0, s>>>(c, e, U, u, cur_key, status, adds, Un, ctr + 1);
+        k_reduce_round<P><<<(unsigned)(slots / RED_WARPS), RED_WARPS * 32, 0, s>>>(c, U, u, 8, cur_key, status, adds,
+                                                                                   scratch, cap, ctr);
+        k_finalize<<<1, 1024, 0, s>>>(c, e, U, u, cur_key, status, adds, Un, ctr + 1, ctr + 2);
         VR_CUDA(cudaGetLastError());
-        VR_CUDA(cudaMemcpyAsync(&hs.p[8], ctr + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaMemcpyAsync(&hs.p[8], ctr + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         VR_CUDA(cudaStreamSynchronize(s));
-        const int64_t un = hs.p[8];
+        if (log_enabled())
+            fprintf(stderr, "[vr] dim%d warp round: %lld -> %lld unfinished\n", P, (long long)u, (long long)hs.p[8]);
         uint32_t* t = U; U = Un; Un = t;
-        const bool stalled = un == u;
-        u = un;
-        if (stalled) break;
+        u = hs.p[8];
     }
+    // Phase 2: one block per remaining column, state kept between rounds; the
+    // first unfinished column always finishes once its budget suffices (no
+    // earlier column can block it), so budgets double every round.
+    int rounds = 0;
     if (u > 0) {
-        const int64_t CAP_S = (int64_t)1 << 22;
-        uint64_t* big = ws.alloc_n<uint64_t>((size_t)2 * CAP_S);
-        k_reduce_seq<P><<<1, 32, 0, s>>>(c, e, U, u, big, big + CAP_S, CAP_S);
-        VR_CUDA(cudaGetLastError());
+        const size_t smem = sizeof(HeavySmem);
+        VR_CUDA(cudaFuncSetAttribute(k_reduce_heavy<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int64_t nslot = u;
+        HeavyState h;
+        h.bcap = std::max<int64_t>((int64_t)1 << 16, std::min<int64_t>((int64_t)1 << 22, ((int64_t)1 << 27) / nslot));
+        h.F = ws.alloc_n<uint64_t>((size_t)nslot * FC);
+        h.B = ws.alloc_n<uint64_t>((size_t)nslot * h.bcap);
+        h.Ks = ws.alloc_n<uint64_t>(nslot);
+        h.fsize = ws.alloc_n<int32_t>(nslot);
+        h.bsize = ws.alloc_n<int64_t>(nslot);
+        h.init = ws.alloc_n<uint8_t>(nslot);
+        h.adds = ws.alloc_n<uint32_t>(nslot);
+        uint32_t* slot_of = ws.alloc_n<uint32_t>(m);
+        k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
+        int budget = 64;
+        while (u > 0) {
+            k_reduce_heavy<P><<<(unsigned)u, HT, smem, s>>>(c, U, u, slot_of, h, budget, keybits, cur_key, status, adds);
+            k_finalize<<<1, 1024, 0, s>>>(c, e, U, u, cur_key, status, adds, Un, ctr + 1, ctr + 2);
+            VR_CUDA(cudaGetLastError());
+            VR_CUDA(cudaMemcpyAsync(&hs.p[8], ctr + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaStreamSynchronize(s));
+            const int64_t un = hs.p[8];
+            const int64_t first = hs.p[9];
+            ++rounds;
+            if (log_enabled())
+                fprintf(stderr, "[vr] dim%d block round %d: budget %d bcap %lld: %lld -> %lld unfinished\n", P,
+                        rounds, budget, (long long)h.bcap, (long long)u, (long long)un);
+            uint32_t* t = U; U = Un; Un = t;
+            const bool stalled = un == u;
+            u = un;
+            if (stalled && first == ST_OVERFLOW) {
+                // the first column outgrew its back buffer: give the remaining
+                // columns the whole arena (they restart from scratch)
+                const int64_t nb = ((int64_t)1 << 27) / (u > 0 ? u : 1);
+                if (nb <= h.bcap) throw Error{VR_ERR_OOM};
+                h.bcap = std::min<int64_t>(nb, (int64_t)1 << 27);
+                h.B = ws.alloc_n<uint64_t>((size_t)u * h.bcap);
+                k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
+                VR_CUDA(cudaGetLastError());
+            }
+            if (budget < (1 << 24)) budget *= 2;
+        }
+    }
+    if (log_enabled()) {
+        VR_CUDA(cudaMemcpyAsync(&hs.p[10], c.pool_used, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaStreamSynchronize(s));
+        fprintf(stderr, "[vr] dim%d reduction: %d block rounds, stored rows %lld of %lld\n", P, rounds,
+                (long long)hs.p[10], (long long)c.pool_cap);
     }
 }
 
@@ -583,6 +1153,11 @@ void run_reduction(const ReduceIn& in, const ReduceOut& out, bool keep_zero, Wor
     VR_CUDA(cudaMemsetAsync(c.hkeys, 0xFF, hcap * sizeof(uint64_t), ws.stream));
     c.hmask = hcap - 1;
     c.err = out.dev_err;
+    c.pool_cap = std::min<int64_t>((int64_t)1 << 24, std::max<int64_t>((int64_t)1 << 16, in.num_cols * 2048));
+    c.pool = ws.alloc_n<uint64_t>((size_t)c.pool_cap);
+    c.pool_used = ws.zeros_n<unsigned long long>(1);
+    c.rc_off = ws.alloc_n<uint64_t>((size_t)in.num_cols);
+    c.rc_len = ws.zeros_n<uint32_t>((size_t)in.num_cols);
     Emit e;
     e.pairs = out.pairs;
     e.num_pairs = out.num_pairs;

@@ -34,6 +34,7 @@ struct Error {
     } while (0)
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+bool log_enabled();  // VR_LOG=1 in the environment: per-stage timings on stderr
 
 // Device-side error word written by kernels (bounded waits, capacity).
 enum DeviceError : int {
