@@ -571,9 +571,10 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
 // ---------------------------------------------------------------------------
 constexpr int HT = 512;          // threads per block
 constexpr int HW = HT / 32;
-constexpr int FC = 8192;         // front capacity
-constexpr int FKEEP = FC - 2048; // front size kept after a spill
+constexpr int FC = 4096;         // front capacity
+constexpr int FKEEP = FC - 1024; // front size kept after a spill
 constexpr int HSTAGE = 1024;     // rows generated or copied per pass (power of two >= HT)
+constexpr int REFILL = FC / 2;   // rows promoted from the back per refill (at most)
 
 struct HeavyState {
     uint64_t* F;       // slots x FC, the front saved between rounds
@@ -584,11 +585,11 @@ struct HeavyState {
     int64_t* bsize;
     uint8_t* init;     // 0: the column has not been started (or must restart)
     uint32_t* adds;
+    unsigned long long* prof;  // VR_LOG only: cycles {refill, lookup, add, resume}, counts {adds, lookups}
 };
 
 struct HeavySmem {
-    uint64_t F[FC];
-    uint64_t F2[2 * FC];
+    uint64_t buf[2][FC];   // the front and its merge target, swapped after each merge
     uint64_t stage[HSTAGE];
     int ws[HW + 1];
     uint32_t hist[256];
@@ -596,10 +597,11 @@ struct HeavySmem {
     int64_t bsize;
     int64_t opos;
     int fsize;
+    int cur;               // which buf holds the front
     int flag;
     int ov[VR_MAX_DIM + 2];
     uint32_t orank;
-    uint64_t sel;     // radix-select result
+    uint64_t sel;          // radix-select result
 };
 
 // exclusive block scan of one int per thread; *total receives the sum
@@ -645,6 +647,16 @@ __device__ void block_bitonic(uint64_t* a, int len) {
         }
 }
 
+// Sort stage[0..cnt) ascending (pads to a power of two with EMPTY).
+__device__ void stage_sort(HeavySmem& S, int cnt) {
+    if (cnt <= 1) return;
+    int len = 2;
+    while (len < cnt) len <<= 1;
+    for (int i = cnt + threadIdx.x; i < len; i += HT) S.stage[i] = EMPTY;
+    __syncthreads();
+    block_bitonic(S.stage, len);
+}
+
 __device__ __forceinline__ int lower_bound_sm(const uint64_t* a, int len, uint64_t x) {
     int lo = 0, hi = len;
     while (lo < hi) {
@@ -665,68 +677,77 @@ __device__ bool heavy_append(HeavySmem& S, uint64_t* B, int64_t bcap, const uint
     return true;
 }
 
-// W <- W + run, run = S.stage[0..b) sorted and unique.  False on B overflow.
-__device__ bool heavy_add_run(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
+// front <- front XOR stage[0..b), stage sorted, unique and entirely below Ks.
+__device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
+    if (b == 0) return true;
     const uint64_t* run = S.stage;
-    const uint64_t Ks = S.Ks;
-    const int lo = lower_bound_sm(run, b, Ks);  // run[0..lo) < Ks <= run[lo..b)
-    if (!heavy_append(S, B, bcap, run + lo, b - lo)) return false;
+    const uint64_t* F = S.buf[S.cur];
+    uint64_t* F2 = S.buf[S.cur ^ 1];
     const int a = S.fsize;
-    // front rows: matches against run[0..lo) decide their position in F2
-    const int chunkF = (a + HT - 1) / HT;
-    const int f0 = min(a, (int)threadIdx.x * chunkF), f1 = min(a, f0 + chunkF);
+    // rows of F below run[0] keep their place
+    const int p0 = lower_bound_sm(F, a, run[0]);
+    for (int i = threadIdx.x; i < p0; i += HT) F2[i] = F[i];
+    const int rest = a - p0;
+    const int chunkF = (rest + HT - 1) / HT;
+    const int f0 = p0 + min(rest, (int)threadIdx.x * chunkF), f1 = min(a, f0 + chunkF);
     int mloc = 0;
     for (int i = f0; i < f1; ++i) {
-        int p = lower_bound_sm(run, lo, S.F[i]);
-        mloc += (p < lo && run[p] == S.F[i]);
+        int q = lower_bound_sm(run, b, F[i]);
+        mloc += (q < b && run[q] == F[i]);
     }
     int mtot;
     int m = block_excl_scan(mloc, S.ws, &mtot);
     for (int i = f0; i < f1; ++i) {
-        const uint64_t x = S.F[i];
-        const int p = lower_bound_sm(run, lo, x);
-        if (p < lo && run[p] == x) { ++m; continue; }
-        S.F2[i + p - 2 * m] = x;
+        const uint64_t x = F[i];
+        const int q = lower_bound_sm(run, b, x);
+        if (q < b && run[q] == x) { ++m; continue; }
+        F2[i + q - 2 * m] = x;
     }
-    const int chunkR = (lo + HT - 1) / HT;
-    const int r0 = min(lo, (int)threadIdx.x * chunkR), r1 = min(lo, r0 + chunkR);
+    const int chunkR = (b + HT - 1) / HT;
+    const int r0 = min(b, (int)threadIdx.x * chunkR), r1 = min(b, r0 + chunkR);
     int mloc2 = 0;
     for (int k = r0; k < r1; ++k) {
-        int p = lower_bound_sm(S.F, a, run[k]);
-        mloc2 += (p < a && S.F[p] == run[k]);
+        const int q = lower_bound_sm(F, a, run[k]);
+        mloc2 += (q < a && F[q] == run[k]);
     }
     int mt2;
     int m2 = block_excl_scan(mloc2, S.ws, &mt2);
     for (int k = r0; k < r1; ++k) {
         const uint64_t y = run[k];
-        const int p = lower_bound_sm(S.F, a, y);
-        if (p < a && S.F[p] == y) { ++m2; continue; }
-        S.F2[k + p - 2 * m2] = y;
+        const int q = lower_bound_sm(F, a, y);
+        if (q < a && F[q] == y) { ++m2; continue; }
+        F2[k + q - 2 * m2] = y;
     }
     __syncthreads();
-    int na = a + lo - 2 * mtot;
+    int na = a + b - 2 * mtot;
+    if (threadIdx.x == 0) S.cur ^= 1;
+    __syncthreads();
     if (na > FKEEP) {  // spill the top of the front to B and lower the split
-        if (!heavy_append(S, B, bcap, S.F2 + FKEEP, na - FKEEP)) return false;
-        if (threadIdx.x == 0) S.Ks = S.F2[FKEEP];
+        if (!heavy_append(S, B, bcap, S.buf[S.cur] + FKEEP, na - FKEEP)) return false;
+        if (threadIdx.x == 0) S.Ks = S.buf[S.cur][FKEEP];
         na = FKEEP;
     }
-    for (int i = threadIdx.x; i < na; i += HT) S.F[i] = S.F2[i];
     if (threadIdx.x == 0) S.fsize = na;
     __syncthreads();
     return true;
 }
 
+// W <- W + run for a sorted, unique run in stage[0..b) (any keys).
+__device__ bool heavy_add_run(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
+    const int lo = lower_bound_sm(S.stage, b, S.Ks);
+    if (!heavy_append(S, B, bcap, S.stage + lo, b - lo)) return false;
+    return heavy_merge_front(S, B, bcap, lo);
+}
+
 // Refill an empty front from B.  Returns false if the column is zero.
 __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
-    const int target = FC / 2;
     for (;;) {
         __syncthreads();
         const int64_t bsz = S.bsize;
         if (bsz == 0) return false;
-        // 1. split T with at most `target` rows below it
-        if (threadIdx.x == 0) S.flag = 0;
+        // 1. split T with at most REFILL rows below it (MSD radix select)
         uint64_t T = EMPTY;
-        if (bsz > target) {
+        if (bsz > REFILL) {
             uint64_t prefix = 0;
             int shift = ((keybits + 7) / 8) * 8 - 8;
             if (shift < 0) shift = 0;
@@ -743,12 +764,10 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
                 if (threadIdx.x == 0) {
                     int d = 0;
                     int64_t bl = below;
-                    while (d < 256 && bl + S.hist[d] <= target) bl += S.hist[d++];
-                    const uint64_t binstart = (prefix & ~((shift + 8 >= 64) ? ~0ull : ((1ull << (shift + 8)) - 1))) |
-                                              ((uint64_t)d << shift);
-                    if (bl > 0) { S.sel = binstart; S.flag = 1; }          // rows below the bin fit
-                    else if (shift == 0) { S.sel = binstart; S.flag = 2; }  // one key, many copies
-                    else { S.sel = binstart; S.flag = 0; }                  // descend into bin d
+                    while (d < 256 && bl + S.hist[d] <= REFILL) bl += S.hist[d++];
+                    const uint64_t hi_mask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1);
+                    S.sel = (prefix & hi_mask) | ((uint64_t)d << shift);
+                    S.flag = bl > 0 ? 1 : (shift == 0 ? 2 : 0);  // 1 done, 2 one key, 0 descend
                     S.ws[HW] = (int)bl;
                 }
                 __syncthreads();
@@ -761,7 +780,8 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
                 __syncthreads();
             }
         }
-        // 2. move rows < T to F2 (tile by tile, so in-place compaction of B is safe)
+        // 2. move rows < T to the spare buffer (tile by tile: B is compacted in place)
+        uint64_t* G = S.buf[S.cur ^ 1];
         int nlt = 0;
         int64_t nge = 0;
         for (int64_t base = 0; base < bsz; base += HT) {
@@ -769,18 +789,17 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
             const uint64_t k = i < bsz ? B[i] : EMPTY;
             const bool lt = i < bsz && k < T;
             const bool ge = i < bsz && !lt;
-            int tl, tg;
-            const int pl = block_excl_scan(lt, S.ws, &tl);
-            const int pg = block_excl_scan(ge, S.ws, &tg);  // syncs: all of this tile was read
-            if (lt && nlt + pl < 2 * FC) S.F2[nlt + pl] = k;
-            if (ge) B[nge + pg] = k;
-            nlt += tl;
-            nge += tg;
+            int tot;
+            const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
+            if (lt && nlt + (packed & 0xFFFF) < FC) G[nlt + (packed & 0xFFFF)] = k;
+            if (ge) B[nge + (packed >> 16)] = k;
+            nlt += tot & 0xFFFF;
+            nge += tot >> 16;
         }
         __syncthreads();
-        if (nlt > 2 * FC) {  // a single key with more copies than fit: keep its parity only
+        if (nlt > FC) {  // a single key with more copies than fit: keep its parity only
             if (threadIdx.x == 0) {
-                S.F[0] = T - 1;
+                S.buf[S.cur][0] = T - 1;
                 S.fsize = (nlt & 1) ? 1 : 0;
                 S.bsize = nge;
                 S.Ks = T;
@@ -791,26 +810,27 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
         }
         int len = 1;
         while (len < nlt) len <<= 1;
-        for (int i = nlt + threadIdx.x; i < len; i += HT) S.F2[i] = EMPTY;
+        for (int i = nlt + threadIdx.x; i < len; i += HT) G[i] = EMPTY;
         __syncthreads();
-        block_bitonic(S.F2, len);
+        block_bitonic(G, len);
         // 3. keep the rows of odd multiplicity
+        uint64_t* F = S.buf[S.cur];
         const int chunk = (nlt + HT - 1) / HT;
         const int c0 = min(nlt, (int)threadIdx.x * chunk), c1 = min(nlt, c0 + chunk);
         int keep = 0;
         for (int i = c0; i < c1; ++i) {
-            if (i > 0 && S.F2[i - 1] == S.F2[i]) continue;
+            if (i > 0 && G[i - 1] == G[i]) continue;
             int e = i;
-            while (e + 1 < nlt && S.F2[e + 1] == S.F2[i]) ++e;
+            while (e + 1 < nlt && G[e + 1] == G[i]) ++e;
             keep += ((e - i + 1) & 1);
         }
         int tk;
         int pos = block_excl_scan(keep, S.ws, &tk);
         for (int i = c0; i < c1; ++i) {
-            if (i > 0 && S.F2[i - 1] == S.F2[i]) continue;
+            if (i > 0 && G[i - 1] == G[i]) continue;
             int e = i;
-            while (e + 1 < nlt && S.F2[e + 1] == S.F2[i]) ++e;
-            if ((e - i + 1) & 1) S.F[pos++] = S.F2[i];
+            while (e + 1 < nlt && G[e + 1] == G[i]) ++e;
+            if ((e - i + 1) & 1) F[pos++] = G[i];
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -823,7 +843,9 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
     }
 }
 
-// W <- W + D_x for the p-simplex x (vertices ascending, diameter rank xr).
+// W <- W + D_x for the p-simplex x (vertices ascending, diameter rank xr):
+// rows at or above the split go straight to B, only the few below it are
+// sorted and merged into the front.
 template <int P>
 __device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x) {
     const int64_t n = c.R.n;
@@ -833,20 +855,27 @@ __device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, in
 #pragma unroll
         for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
         uint32_t rt = x.r;
+        uint64_t key = EMPTY;
         if (ok) {
 #pragma unroll
             for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
             ok = rt <= c.thr;
+            if (ok) key = row_key<P>(c, x, w, rt);
         }
+        const bool lt = ok && key < S.Ks;
+        const bool ge = ok && !lt;
         int tot;
-        const int pos = block_excl_scan(ok, S.ws, &tot);
-        if (ok) S.stage[pos] = row_key<P>(c, x, w, rt);
-        int len = 2;
-        while (len < tot) len <<= 1;
-        for (int i = tot + threadIdx.x; i < len; i += HT) S.stage[i] = EMPTY;
+        const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
+        const int nlt = tot & 0xFFFF, nge = tot >> 16;
+        const int64_t bs = S.bsize;
+        if (bs + nge > bcap) return false;
+        if (ge) B[bs + (packed >> 16)] = key;
+        if (lt) S.stage[packed & 0xFFFF] = key;
         __syncthreads();
-        block_bitonic(S.stage, len);
-        if (!heavy_add_run(S, B, bcap, tot)) return false;
+        if (threadIdx.x == 0) S.bsize = bs + nge;
+        __syncthreads();
+        stage_sort(S, nlt);
+        if (!heavy_merge_front(S, B, bcap, nlt)) return false;
     }
     return true;
 }
@@ -954,24 +983,33 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
     uint32_t adds;
     bool ok = true;
     if (!hs.init[slot]) {
-        if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.Ks = EMPTY; }
+        if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.Ks = EMPTY; S.cur = 0; }
         __syncthreads();
         adds = 0;
         ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, s);
     } else {
-        if (threadIdx.x == 0) { S.fsize = hs.fsize[slot]; S.bsize = hs.bsize[slot]; S.Ks = hs.Ks[slot]; }
+        if (threadIdx.x == 0) { S.fsize = hs.fsize[slot]; S.bsize = hs.bsize[slot]; S.Ks = hs.Ks[slot]; S.cur = 0; }
         adds = hs.adds[slot];
         __syncthreads();
-        for (int i = threadIdx.x; i < S.fsize; i += HT) S.F[i] = hs.F[slot * FC + i];
+        for (int i = threadIdx.x; i < S.fsize; i += HT) S.buf[0][i] = hs.F[slot * FC + i];
         __syncthreads();
     }
     uint64_t key = ok ? EMPTY : 0;  // 0: no consistent state yet, the smallest (always valid) bound
     uint8_t st = ST_COMPLETE;
     int done = 0;
+    long long t0 = clock64(), t_ref = 0, t_look = 0, t_add = 0, n_look = 0;
+    const long long t_resume = t0;
     while (ok) {
+        long long ta = clock64();
         if (S.fsize == 0 && !heavy_refill(S, B, keybits)) { key = EMPTY; break; }  // zero column
-        key = S.F[0];
-        if (!heavy_owner<P>(c, S, key, self_key)) break;  // pivot unknown: complete
+        long long tb = clock64();
+        t_ref += tb - ta;
+        key = S.buf[S.cur][0];
+        const bool owned = heavy_owner<P>(c, S, key, self_key);
+        long long tc = clock64();
+        t_look += tc - tb;
+        ++n_look;
+        if (!owned) break;  // pivot unknown: complete
         if (done >= budget) { st = ST_BUDGET; break; }
         if (S.flag == 1) {
             const int64_t opos = S.opos;
@@ -992,9 +1030,18 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
         ++adds;
         ++done;
         __syncthreads();
+        t_add += clock64() - tc;
+    }
+    if (hs.prof && threadIdx.x == 0) {
+        atomicAdd(hs.prof + 0, (unsigned long long)t_ref);
+        atomicAdd(hs.prof + 1, (unsigned long long)t_look);
+        atomicAdd(hs.prof + 2, (unsigned long long)t_add);
+        atomicAdd(hs.prof + 3, (unsigned long long)(clock64() - t_resume - t_ref - t_look - t_add));
+        atomicAdd(hs.prof + 4, (unsigned long long)done);
+        atomicAdd(hs.prof + 5, (unsigned long long)n_look);
     }
     if (!ok) st = ST_OVERFLOW;  // key holds the last consistent pivot, a valid bound
-    for (int i = threadIdx.x; i < S.fsize && ok; i += HT) hs.F[slot * FC + i] = S.F[i];
+    for (int i = threadIdx.x; i < S.fsize && ok; i += HT) hs.F[slot * FC + i] = S.buf[S.cur][i];
     if (threadIdx.x == 0) {
         hs.fsize[slot] = S.fsize;
         hs.bsize[slot] = S.bsize;
@@ -1092,6 +1139,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         h.bsize = ws.alloc_n<int64_t>(nslot);
         h.init = ws.alloc_n<uint8_t>(nslot);
         h.adds = ws.alloc_n<uint32_t>(nslot);
+        h.prof = log_enabled() ? ws.zeros_n<unsigned long long>(8) : nullptr;
         uint32_t* slot_of = ws.alloc_n<uint32_t>(m);
         k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
         int budget = 64;
@@ -1121,6 +1169,16 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 VR_CUDA(cudaGetLastError());
             }
             if (budget < (1 << 24)) budget *= 2;
+        }
+        if (h.prof) {
+            VR_CUDA(cudaMemcpyAsync(&hs.p[16], h.prof, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaStreamSynchronize(s));
+            const double ad = hs.p[20] ? (double)hs.p[20] : 1.0, lk = hs.p[21] ? (double)hs.p[21] : 1.0;
+            fprintf(stderr,
+                    "[vr] dim%d block engine: %lld additions, %lld lookups; cycles/add %.0f, cycles/lookup %.0f, "
+                    "refill total %lld, other total %lld\n",
+                    P, (long long)hs.p[20], (long long)hs.p[21], hs.p[18] / ad, hs.p[17] / lk, (long long)hs.p[16],
+                    (long long)hs.p[19]);
         }
     }
     if (log_enabled()) {
