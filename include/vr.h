@@ -82,6 +82,12 @@ typedef struct {
     int64_t pairs;       /* persistence pairs of dimension p, zero-length included        */
     int64_t essential;   /* classes that never die                                        */
     int64_t emitted;     /* entries written to vr_result.pairs[p]                          */
+    int64_t cofacets_scanned; /* cofacets examined by the apparent-pair search                 */
+    int64_t lookups;     /* diameter-rank entries read by the fused filtration/apparent kernel */
+    float ms_filtration; /* CUDA-event time of the fused filtration/clearing/apparent kernel
+                            (p = 0: diameter ranks and enclosing radius)                      */
+    float ms_sort;       /* radix sort of the non-apparent columns (p >= 1)                   */
+    float ms_reduce;     /* Z/2 reduction (p = 0: spanning tree and elder rule)               */
 } vr_stats;
 
 typedef struct {

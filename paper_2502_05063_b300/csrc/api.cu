@@ -198,26 +198,37 @@ bool log_enabled() {
     return on;
 }
 
+// CUDA events on the caller's stream around each stage; the durations go to
+// vr_result.stats and, with VR_LOG=1, to stderr.
 struct StageLog {
-    bool on;
     cudaStream_t s;
     std::vector<std::pair<std::string, cudaEvent_t>> ev;
-    explicit StageLog(cudaStream_t st) : on(log_enabled()), s(st) { mark("start"); }
+    explicit StageLog(cudaStream_t st) : s(st) { mark("start"); }
     void mark(const std::string& name) {
-        if (!on) return;
         cudaEvent_t e;
-        cudaEventCreate(&e);
+        if (cudaEventCreate(&e) != cudaSuccess) return;
         cudaEventRecord(e, s);
         ev.emplace_back(name, e);
     }
-    ~StageLog() {
-        if (!on) return;
-        cudaStreamSynchronize(s);
+    cudaEvent_t find(const std::string& name) const {
+        for (auto it = ev.rbegin(); it != ev.rend(); ++it)  // the last mark of that name
+            if (it->first == name) return it->second;
+        return nullptr;
+    }
+    float between(const std::string& a, const std::string& b) const {  // after a synchronisation
+        cudaEvent_t ea = find(a), eb = find(b);
+        float ms = 0.0f;
+        if (ea && eb && cudaEventElapsedTime(&ms, ea, eb) != cudaSuccess) ms = 0.0f;
+        return ms;
+    }
+    void print() const {
         for (size_t i = 1; i < ev.size(); ++i) {
             float ms = 0;
             cudaEventElapsedTime(&ms, ev[i - 1].second, ev[i].second);
             fprintf(stderr, "[vr] %-24s %9.3f ms\n", ev[i].first.c_str(), ms);
         }
+    }
+    ~StageLog() {
         for (auto& e : ev) cudaEventDestroy(e.second);
     }
 };
@@ -355,13 +366,14 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
             ao.counters = cnt;
             ao.capacity = cap;
             ao.dev_err = dev_err;
+            log.mark(stage_name("launch apparent", p));
             launch_filtration_apparent(p, R, B, thr, clear, cb, rank_bits, ncand, ao, s);
+            log.mark(stage_name("apparent", p));
             VR_CUDA(cudaMemcpyAsync(hs.p, cnt, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             VR_CUDA(cudaStreamSynchronize(s));
             if (hs.p[4] <= cap) break;
             cap = hs.p[4];  // rerun with room for every non-apparent column
         }
-        log.mark(stage_name("apparent", p));
         check_dev_err(dev_err, s);
         vr_stats& st = res->stats[p];
         st.candidates = (int64_t)ncand;
@@ -372,6 +384,11 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         const int64_t nna = hs.p[4];
         const int64_t nzero = hs.p[5];
         st.reduced = nna;
+        // rank-matrix entries the fused kernel reads: diameters of the candidates,
+        // p+1 per examined cofacet, all pairs of t for each facet test
+        st.lookups = (int64_t)ncand * (p + 1) * p / 2 + hs.p[6] * (p + 1) + hs.p[7] * (p + 2) * (p + 1) / 2;
+        st.cofacets_scanned = hs.p[6];
+        log.mark(stage_name("launch sort", p));
         radix_sort_u64(ws, keys, nullptr, nna, rank_bits + cb);
         log.mark(stage_name("sort", p));
         PairRec* pr = ws.alloc_n<PairRec>(nna > 0 ? nna : 1);
@@ -392,6 +409,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         out.clear_next = clear_next;
         out.counters = rc + 1;
         out.dev_err = dev_err;
+        log.mark(stage_name("launch reduce", p));
         run_reduction(in, out, keep_zero, ws, hs);
         log.mark(stage_name("reduce", p));
         VR_CUDA(cudaMemcpyAsync(hs.p + 8, rc, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -409,6 +427,15 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         log.mark(stage_name("emit", p));
         clear = clear_next;
     }
+    VR_CUDA(cudaStreamSynchronize(s));
+    res->stats[0].ms_filtration = log.between("start", "ranks");
+    res->stats[0].ms_reduce = log.between("ranks", "h0");
+    for (int p = 1; p <= dmax; ++p) {
+        res->stats[p].ms_filtration = log.between(stage_name("launch apparent", p), stage_name("apparent", p));
+        res->stats[p].ms_sort = log.between(stage_name("launch sort", p), stage_name("sort", p));
+        res->stats[p].ms_reduce = log.between(stage_name("launch reduce", p), stage_name("reduce", p));
+    }
+    if (log_enabled()) log.print();
     guard.r = nullptr;
     return res;
 }

@@ -51,7 +51,7 @@ k_filtration_apparent(RankMatrix R, Binom B, uint32_t thr, const uint32_t* __res
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t n = R.n;
-    unsigned long long c_above = 0, c_cleared = 0, c_kept = 0, c_app = 0;
+    unsigned long long c_above = 0, c_cleared = 0, c_kept = 0, c_app = 0, c_scan = 0, c_facet = 0;
 
     for (uint64_t chunk = warp; chunk * 32 < num_cand; chunk += nwarps) {
         const uint64_t c = chunk * 32 + lane;
@@ -87,8 +87,14 @@ k_filtration_apparent(RankMatrix R, Binom B, uint32_t thr, const uint32_t* __res
 #pragma unroll
                 for (int a = 0; a < NV; ++a) ok = ok && (R(sv[a], w) <= sr);
                 const uint32_t b = __ballot_sync(0xffffffffu, ok);
-                if (b) { wf = base - (__ffs(b) - 1); break; }
+                if (b) {
+                    wf = base - (__ffs(b) - 1);
+                    c_scan += base - wf + 1;  // vertices w examined up to the hit
+                    break;
+                }
+                c_scan += base >= 31 ? 32 : base + 1;
             }
+            if (wf >= 0) ++c_facet;
             bool apparent = false;
             if (wf >= 0) {
                 // t = s + wf; lane k tests pair k of t for rank == diam
@@ -156,6 +162,8 @@ k_filtration_apparent(RankMatrix R, Binom B, uint32_t thr, const uint32_t* __res
         if (c_cleared) atomicAdd(o.counters + 1, c_cleared);
         if (c_kept) atomicAdd(o.counters + 2, c_kept);
         if (c_app) atomicAdd(o.counters + 3, c_app);
+        if (c_scan) atomicAdd(o.counters + 6, c_scan);    // counted identically on every lane
+        if (c_facet) atomicAdd(o.counters + 7, c_facet);
     }
 }
 

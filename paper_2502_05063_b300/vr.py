@@ -43,11 +43,14 @@ class Pair(ctypes.Structure):
 
 
 STAT_FIELDS = ["candidates", "above_threshold", "cleared", "columns", "apparent", "reduced",
-               "additions", "pairs", "essential", "emitted"]
+               "additions", "pairs", "essential", "emitted", "cofacets_scanned", "lookups"]
+
+
+TIME_FIELDS = ["ms_filtration", "ms_sort", "ms_reduce"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_int64) for f in STAT_FIELDS]
+    _fields_ = [(f, ctypes.c_int64) for f in STAT_FIELDS] + [(f, ctypes.c_float) for f in TIME_FIELDS]
 
 
 class Result(ctypes.Structure):
@@ -141,7 +144,7 @@ class Barcodes:
                 self.critical_edges.append(e.reshape(m, 4).copy())
             else:
                 self.critical_edges.append(None)
-            self.stats.append({f: getattr(res.stats[p], f) for f in STAT_FIELDS})
+            self.stats.append({f: getattr(res.stats[p], f) for f in STAT_FIELDS + TIME_FIELDS})
 
 
 def barcodes(points=None, dists=None, n=None, dmax=1, threshold=np.inf, flags=0, stream=None) -> Barcodes:

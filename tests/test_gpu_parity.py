@@ -218,7 +218,8 @@ def test_repeatable(vr):
         again = vr.barcodes(points=pts, dmax=2)
         for p in range(3):
             assert rows_gpu(first, p) == rows_gpu(again, p)
-            assert first.stats[p] == again.stats[p]
+            counts = lambda st: {k: v for k, v in st.items() if not k.startswith("ms_")}
+            assert counts(first.stats[p]) == counts(again.stats[p])
 
 
 # --------------------------------------------------------------------------
