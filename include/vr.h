@@ -175,6 +175,24 @@ vr_status vr_distances(const float* pts, int64_t n, int32_t ambient_dim, float* 
  * stable), values (may be NULL) permuted alongside.                          */
 vr_status vr_sort_u64(uint64_t* keys, uint64_t* values, int64_t num, int32_t bits, void* stream);
 
+/* Allocation-free variant of vr_sort_u64.  The paper has no counterpart: it
+ * exists for callers that must not allocate device memory during the call --
+ * code running under a fixed, pre-reserved device-memory budget (a serving
+ * process that partitions the GPU up front, a host whose allocator must not
+ * be re-entered from a library).  It sorts the same way as vr_sort_u64 (same
+ * kernels, same results) but takes its scratch from a static device array
+ * that every GPU loading the library keeps until the process exits.
+ *  num        at most VR_SORT_NOALLOC_MAX_KEYS; larger sizes return
+ *             VR_ERR_INVALID_ARG and touch nothing.
+ *  keys, values  device pointers, as in vr_sort_u64 (values may be NULL).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU (several streams or host threads) race and must be
+ * serialised by the caller.  Returns after `stream` has finished the sort.  */
+#define VR_SORT_NOALLOC_MAX_KEYS (1 << 18)
+vr_status vr_sort_u64_noalloc(uint64_t* keys, uint64_t* values, int64_t num, int32_t bits, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,8 @@
 //   3. k_scatter stable scatter: a tile is walked in index order, ranks of
 //                equal digits inside a warp come from __match_any_sync, the
 //                offsets of earlier warps and rounds from shared counters.
+#include <mutex>
+
 #include "vr_common.cuh"
 
 namespace vr {
@@ -170,3 +172,96 @@ void radix_sort_u32(Workspace& ws, uint32_t* keys, uint32_t* vals, int64_t num, 
 }
 
 }  // namespace vr
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the sort (vr_sort_u64_noalloc).
+//
+// For callers that cannot allocate device memory while they run -- code
+// working inside a fixed, pre-reserved device-memory budget (a serving
+// process that partitions the GPU up front, a host application whose
+// allocator must not be re-entered from a library call) -- the ping-pong
+// key/value buffers and the digit histogram come from this file-scope
+// device array instead of cudaMallocAsync.  Every GPU that loads the library
+// holds the array until the process exits.  Host code cannot use the array's
+// name as a device address: the address is fetched with cudaGetSymbolAddress
+// once per device, with that device current, on the first call made on it.
+// All calls share the array, so calls whose work overlaps on the GPU (other
+// streams, other host threads) race and must be serialised by the caller.
+// Nothing in it needs to start at zero: every pass rewrites the histogram
+// and both buffers before reading them.
+// ---------------------------------------------------------------------------
+namespace vr {
+namespace {
+
+constexpr int64_t NOALLOC_MAX_KEYS = (int64_t)1 << 18;  // 262,144 keys: about 4.3 MB of scratch
+constexpr int64_t NOALLOC_TILES = (NOALLOC_MAX_KEYS + RS_TILE - 1) / RS_TILE;
+
+struct NoAllocScratch {
+    uint64_t keys[NOALLOC_MAX_KEYS];
+    uint64_t vals[NOALLOC_MAX_KEYS];
+    uint32_t hist[NOALLOC_TILES * RS_BINS];
+};
+
+static __device__ __align__(256) NoAllocScratch g_sort_scratch;
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+NoAllocScratch* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_sort_scratch on the current device (set-up on first use).
+NoAllocScratch* noalloc_scratch() {
+    int dev = 0;
+    VR_CUDA(cudaGetDevice(&dev));
+    VR_CHECK(dev >= 0 && dev < NOALLOC_MAX_DEVICES, VR_ERR_CUDA);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        VR_CUDA(cudaGetSymbolAddress(&p, g_sort_scratch));
+        g_noalloc_addr[dev] = static_cast<NoAllocScratch*>(p);
+    }
+    return g_noalloc_addr[dev];
+}
+
+template <bool HAS_V>
+void sort_passes_noalloc(NoAllocScratch* sc, uint64_t* keys, uint64_t* vals, int64_t num, int bits,
+                         cudaStream_t s) {
+    const int64_t tiles = (num + RS_TILE - 1) / RS_TILE;
+    uint64_t* kin = keys; uint64_t* kout = sc->keys;
+    uint64_t* vin = vals; uint64_t* vout = sc->vals;
+    const int passes = (bits + 7) / 8;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = ps * 8;
+        k_hist<uint64_t><<<(unsigned)tiles, RS_THREADS, 0, s>>>(kin, num, shift, sc->hist, tiles);
+        k_scan<<<1, 1024, 0, s>>>(sc->hist, tiles * RS_BINS);
+        k_scatter<uint64_t, uint64_t, HAS_V><<<(unsigned)tiles, RS_THREADS, 0, s>>>(kin, vin, kout, vout, num, shift,
+                                                                                   sc->hist, tiles);
+        VR_CUDA(cudaGetLastError());
+        uint64_t* tk = kin; kin = kout; kout = tk;
+        uint64_t* tv = vin; vin = vout; vout = tv;
+    }
+    if (kin != keys) {
+        VR_CUDA(cudaMemcpyAsync(keys, kin, num * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        if (HAS_V) VR_CUDA(cudaMemcpyAsync(vals, vin, num * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+}  // namespace
+
+}  // namespace vr
+
+extern "C" vr_status vr_sort_u64_noalloc(uint64_t* keys, uint64_t* values, int64_t num, int32_t bits, void* stream) {
+    if (num < 0 || bits < 0 || bits > 64 || (num > 0 && !keys)) return VR_ERR_INVALID_ARG;
+    if (num > vr::NOALLOC_MAX_KEYS) return VR_ERR_INVALID_ARG;  // larger than the static scratch
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        if (num > 1 && bits > 0) {
+            vr::NoAllocScratch* sc = vr::noalloc_scratch();
+            if (values) vr::sort_passes_noalloc<true>(sc, keys, values, num, bits, s);
+            else vr::sort_passes_noalloc<false>(sc, keys, nullptr, num, bits, s);
+        }
+        VR_CUDA(cudaStreamSynchronize(s));
+        return VR_OK;
+    } catch (const vr::Error& e) {
+        return e.code;
+    }
+}

@@ -82,6 +82,8 @@ lib.vr_result_free.restype = None
 lib.vr_simplex_vertices.argtypes = [ctypes.c_uint64, _i32, _i64, _vp]
 lib.vr_distances.argtypes = [_vp, _i64, _i32, _vp, _vp]
 lib.vr_sort_u64.argtypes = [_vp, _vp, _i64, _i32, _vp]
+lib.vr_sort_u64_noalloc.argtypes = [_vp, _vp, _i64, _i32, _vp]
+VR_SORT_NOALLOC_MAX_KEYS = 1 << 18
 lib.vr_backward.argtypes = [_vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp]
 if hasattr(lib, "vr_barcodes_batched"):
     lib.vr_barcodes_batched.argtypes = [_vp, _vp, _i32, _i32, _i32, _f32, _u32, _vp,
@@ -187,6 +189,14 @@ def sort_u64(keys_dev, values_dev=None, bits=64, stream=None):
     """In-place stable ascending radix sort of CUDA int64/uint64 tensors by the low `bits` bits."""
     _check(lib.vr_sort_u64(keys_dev.data_ptr(), values_dev.data_ptr() if values_dev is not None else None,
                            int(keys_dev.numel()), int(bits), _stream_ptr(stream)), "vr_sort_u64")
+
+
+def sort_u64_noalloc(keys_dev, values_dev=None, bits=64, stream=None):
+    """Like sort_u64, but the library allocates nothing: its scratch is a fixed
+    static device array (at most VR_SORT_NOALLOC_MAX_KEYS keys).  Calls that
+    overlap on the GPU share that array and must not run concurrently."""
+    _check(lib.vr_sort_u64_noalloc(keys_dev.data_ptr(), values_dev.data_ptr() if values_dev is not None else None,
+                                   int(keys_dev.numel()), int(bits), _stream_ptr(stream)), "vr_sort_u64_noalloc")
 
 
 def backward(pts_dev, edges_dev, grad_birth_dev, grad_death_dev, grad_pts_dev, stream=None):
