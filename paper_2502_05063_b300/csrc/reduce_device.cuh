@@ -1,0 +1,845 @@
+// reduce_device.cuh -- device-side pieces of the Z/2 reduction shared by the
+// single-cloud schedule (reduce.cu) and the batched kernel (batched.cu): row
+// keys, coboundary generation, pivot lookup (hash of finished columns, then
+// apparent pairs recomputed from Def 5.3.4), the warp engine for light columns
+// and the block engine (front/back split) for heavy columns.  See reduce.cu for
+// the method and its justification.
+#pragma once
+
+#include "vr_common.cuh"
+
+namespace vr {
+namespace {
+
+
+constexpr uint64_t EMPTY = ~0ull;
+constexpr int RED_WARPS = 4;      // warps per block, round mode
+constexpr int STAGE = 1024;       // per-warp shared staging of generated rows
+constexpr uint8_t ST_COMPLETE = 0, ST_BUDGET = 1, ST_OVERFLOW = 2;
+
+struct Ctx {
+    RankMatrix R;
+    Binom B;
+    uint32_t thr;
+    int cb, rcb;
+    uint64_t cmask, rcmask, rmask;
+    const uint64_t* cols;
+    int64_t num_cols;
+    uint64_t* hkeys;   // pivot cidx (EMPTY = free)
+    uint32_t* hvals;   // column position
+    uint64_t hmask;
+    int* err;
+    // finished columns that needed additions keep their reduced form R_j here,
+    // so a later column adds R_j (standard reduction) instead of D_j
+    uint64_t* pool;
+    unsigned long long* pool_used;
+    int64_t pool_cap;
+    uint64_t* rc_off;  // per column position
+    uint32_t* rc_len;  // 0: the column is its own coboundary D_j
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull; x ^= x >> 33;
+    return x;
+}
+
+template <int P>
+struct Simplex {
+    int v[P + 1];   // ascending
+    uint32_t r;     // diameter rank
+    uint64_t cidx;
+};
+
+template <int P>
+__device__ __forceinline__ void load_col(const Ctx& c, uint64_t key, Simplex<P>& s) {
+    s.cidx = key & c.cmask;
+    s.r = (uint32_t)((~(key >> c.cb)) & c.rmask);
+    decode_simplex<P>(c.B, s.cidx, c.R.n - 1, s.v);
+}
+
+template <int P>
+__device__ __forceinline__ uint64_t col_key(const Ctx& c, const Simplex<P>& s) {
+    return ((~(uint64_t)s.r & c.rmask) << c.cb) | s.cidx;
+}
+
+// index of s + {w}, w not a vertex of s (eq. 5.6 with w inserted in place)
+template <int P>
+__device__ __forceinline__ uint64_t cofacet_cidx(const Binom& B, const int* v, int64_t w) {
+    uint64_t ct = 0;
+    int k = 0;
+    bool placed = false;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+        if (!placed && w < v[a]) { ct += B(w, k + 1); ++k; placed = true; }
+        ct += B(v[a], k + 1);
+        ++k;
+    }
+    if (!placed) ct += B(w, k + 1);
+    return ct;
+}
+
+template <int P>
+__device__ __forceinline__ uint64_t row_key(const Ctx& c, const Simplex<P>& s, int64_t w, uint32_t rt) {
+    return ((uint64_t)rt << c.rcb) | (c.rcmask - cofacet_cidx<P>(c.B, s.v, w));
+}
+
+// Pivot of the unreduced column D_s: smallest (rank asc, w desc) cofacet.
+template <int P>
+__device__ uint64_t warp_column_pivot(const Ctx& c, const Simplex<P>& s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = c.R.n;
+    uint32_t brt = 0xFFFFFFFFu;
+    int64_t bw = -1;
+    for (int64_t base = n - 1; base >= 0; base -= 32) {
+        const int64_t w = base - lane;
+        bool ok = w >= 0;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) ok = ok && (w != s.v[a]);
+        if (ok) {
+            uint32_t rt = s.r;
+#pragma unroll
+            for (int a = 0; a <= P; ++a) rt = max(rt, c.R(s.v[a], w));
+            if (rt <= c.thr && rt < brt) { brt = rt; bw = w; }  // w only decreases per lane
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint32_t ort = __shfl_xor_sync(0xffffffffu, brt, o);
+        int64_t ow = __shfl_xor_sync(0xffffffffu, bw, o);
+        if (ort < brt || (ort == brt && ow > bw)) { brt = ort; bw = ow; }
+    }
+    if (bw < 0) return EMPTY;
+    return row_key<P>(c, s, bw, brt);
+}
+
+// Bitonic sort of stage[0..len) (len a power of two >= 32) by one warp.
+__device__ void warp_bitonic(uint64_t* stage, int len) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= len; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < len; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t a = stage[i], b = stage[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { stage[i] = b; stage[ixj] = a; }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t len, uint64_t x) {
+    int64_t lo = 0, hi = len;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// out = in XOR S (symmetric difference of two sorted sets), returns the new
+// size or -1 if it would exceed cap.
+__device__ int64_t warp_xor_merge(const uint64_t* in, int64_t a, const uint64_t* S, int64_t b, uint64_t* out,
+                                  int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    int64_t matched = 0;
+    bool over = false;
+    for (int64_t base = 0; base < a; base += 32) {
+        const int64_t i = base + lane;
+        const uint64_t x = i < a ? in[i] : EMPTY;
+        int64_t bs = 0;
+        bool m = false;
+        if (i < a) {
+            bs = lower_bound_u64(S, b, x);
+            m = bs < b && S[bs] == x;
+        }
+        const uint32_t mb = __ballot_sync(0xffffffffu, m);
+        const int64_t mw = matched + __popc(mb & lt);
+        if (i < a && !m) {
+            const int64_t pos = i + bs - 2 * mw;
+            if (pos < cap) out[pos] = x; else over = true;
+        }
+        matched += __popc(mb);
+    }
+    int64_t matched2 = 0;
+    for (int64_t base = 0; base < b; base += 32) {
+        const int64_t k = base + lane;
+        const uint64_t y = k < b ? S[k] : EMPTY;
+        int64_t bw = 0;
+        bool m = false;
+        if (k < b) {
+            bw = lower_bound_u64(in, a, y);
+            m = bw < a && in[bw] == y;
+        }
+        const uint32_t mb = __ballot_sync(0xffffffffu, m);
+        const int64_t ms = matched2 + __popc(mb & lt);
+        if (k < b && !m) {
+            const int64_t pos = k + bw - 2 * ms;
+            if (pos < cap) out[pos] = y; else over = true;
+        }
+        matched2 += __popc(mb);
+    }
+    __syncwarp();
+    if (__any_sync(0xffffffffu, over)) return -1;
+    return a + b - 2 * matched;
+}
+
+// W <- W + D_x.  W lives in *W (size a) and the spare buffer *spare; the
+// pointers are swapped as pieces are merged.  Returns the new size or -1.
+template <int P>
+__device__ int64_t warp_add_coboundary(const Ctx& c, const Simplex<P>& x, uint64_t* stage, uint64_t*& W,
+                                       uint64_t*& spare, int64_t a, int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t n = c.R.n;
+    int64_t base = n - 1;
+    while (base >= 0) {
+        int fill = 0;
+        while (base >= 0 && fill <= STAGE - 32) {
+            const int64_t w = base - lane;
+            bool ok = w >= 0;
+#pragma unroll
+            for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
+            uint32_t rt = x.r;
+            if (ok) {
+#pragma unroll
+                for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
+                ok = rt <= c.thr;
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, ok);
+            if (ok) stage[fill + __popc(b & lt)] = row_key<P>(c, x, w, rt);
+            fill += __popc(b);
+            base -= 32;
+        }
+        int len = 32;
+        while (len < fill) len <<= 1;
+        for (int i = fill + lane; i < len; i += 32) stage[i] = EMPTY;
+        __syncwarp();
+        warp_bitonic(stage, len);
+        const int64_t na = warp_xor_merge(W, a, stage, fill, spare, cap);
+        __syncwarp();
+        if (na < 0) return -1;
+        uint64_t* t = W; W = spare; spare = t;
+        a = na;
+    }
+    return a;
+}
+
+// Position of the finished column whose pivot is the (p+1)-simplex ct, or -1;
+// one warp probes 32 slots of the open-addressing table at a time.
+__device__ int64_t warp_hash_find(const Ctx& c, uint64_t ct) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t slot0 = mix64(ct) & c.hmask;
+    for (uint64_t probe = 0; probe <= c.hmask; probe += 32) {
+        const uint64_t sl = (slot0 + probe + lane) & c.hmask;
+        const uint64_t k = c.hkeys[sl];
+        const uint32_t hit = __ballot_sync(0xffffffffu, k == ct);
+        const uint32_t emp = __ballot_sync(0xffffffffu, k == EMPTY);
+        if (hit && (!emp || __ffs(hit) < __ffs(emp)))
+            return (int64_t)__shfl_sync(0xffffffffu, c.hvals[sl], __ffs(hit) - 1);
+        if (emp) break;
+    }
+    return -1;
+}
+
+// Owner of pivot row key rk among the columns before `self_key` in order:
+// returns true and fills `o`, or false if rk is no known pivot.
+template <int P>
+__device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex<P>& o, int64_t& opos) {
+    constexpr int NT = P + 2;
+    constexpr int NPAIR = NT * (NT - 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = c.R.n;
+    const uint32_t rt = (uint32_t)(rk >> c.rcb);
+    const uint64_t ct = c.rcmask - (rk & c.rcmask);
+    // 1. pivots of reduced columns
+    {
+        const int64_t pos = warp_hash_find(c, ct);
+        if (pos >= 0) {
+            const uint64_t okey = c.cols[pos];
+            if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL);
+            load_col<P>(c, okey, o);
+            opos = pos;
+            return true;
+        }
+    }
+    // 2. apparent pairs (Def 5.3.4), recomputed
+    int tv[NT];
+    decode_simplex<P + 1>(c.B, ct, n - 1, tv);
+    bool eq = false;
+    int pi = 0, pj = 0;
+    if (lane < NPAIR) {
+        int k = lane;
+        pi = 1;
+        while (k >= pi) { k -= pi; ++pi; }
+        pj = k;
+        eq = c.R(tv[pi], tv[pj]) == rt;
+    }
+    int drop = -1;
+#pragma unroll
+    for (int m = NT - 1; m >= 0; --m) {  // largest vertex first = smallest facet index
+        if (drop < 0 && __ballot_sync(0xffffffffu, eq && pi != m && pj != m)) drop = m;
+    }
+    if (drop < 0) return false;
+    int k = 0;
+#pragma unroll
+    for (int q = 0; q < NT; ++q)
+        if (q != drop) o.v[k++] = tv[q];
+    const int64_t wd = tv[drop];
+    for (int64_t base = n - 1; base > wd; base -= 32) {
+        const int64_t w = base - lane;
+        bool ok = w > wd;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (w != o.v[q]);
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (c.R(o.v[q], w) <= rt);
+        if (__ballot_sync(0xffffffffu, ok)) return false;  // an older cofacet of s' exists
+    }
+    o.r = rt;
+    uint64_t cs = 0;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) cs += c.B(o.v[q], q + 1);
+    o.cidx = cs;
+    if (!(col_key<P>(c, o) < self_key)) atomicExch(c.err, DEV_INTERNAL);
+    opos = -1;
+    return true;
+}
+
+// W <- W + R_o: the stored reduced column of a finished column, or its
+// coboundary when none is stored (apparent columns, zero-addition columns).
+template <int P>
+__device__ int64_t warp_add_owner(const Ctx& c, const Simplex<P>& o, int64_t opos, uint64_t* stage, uint64_t*& W,
+                                  uint64_t*& spare, int64_t a, int64_t cap) {
+    if (opos >= 0) {
+        const uint32_t len = c.rc_len[opos];
+        if (len) {
+            const int64_t na = warp_xor_merge(W, a, c.pool + c.rc_off[opos], len, spare, cap);
+            __syncwarp();
+            if (na < 0) return -1;
+            uint64_t* t = W; W = spare; spare = t;
+            return na;
+        }
+    }
+    return warp_add_coboundary<P>(c, o, stage, W, spare, a, cap);
+}
+
+// Keep the reduced column of position j (W[0..a)) for later additions.
+__device__ void store_reduced(const Ctx& c, int64_t j, const uint64_t* W, int64_t a) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(c.pool_used, (unsigned long long)a);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    const bool fits = (int64_t)(off + a) <= c.pool_cap && a <= 0xFFFFFFFFll;
+    if (fits)
+        for (int64_t i = lane; i < a; i += 32) c.pool[off + i] = W[i];
+    __syncwarp();
+    if (lane == 0) {
+        c.rc_off[j] = off;
+        c.rc_len[j] = fits ? (uint32_t)a : 0u;  // no room: later additions regenerate D_j
+    }
+}
+
+// Reduce column j (position in cols) against the known pivots.  At most
+// `budget` additions; on completion with additions the result is stored.
+template <int P>
+__device__ void reduce_one(const Ctx& c, int64_t j, int budget, uint64_t* stage, uint64_t* bufA, uint64_t* bufB,
+                           int64_t cap, uint64_t& out_key, uint8_t& out_status, uint32_t& out_adds) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t self_key = c.cols[j];
+    Simplex<P> s, o;
+    int64_t opos = -1;
+    load_col<P>(c, self_key, s);
+    uint64_t piv = warp_column_pivot<P>(c, s);
+    out_adds = 0;
+    if (lane == 0) c.rc_len[j] = 0;
+    if (piv == EMPTY) { out_key = EMPTY; out_status = ST_COMPLETE; return; }
+    if (!warp_owner<P>(c, piv, self_key, o, opos)) { out_key = piv; out_status = ST_COMPLETE; return; }
+    uint64_t* W = bufA;
+    uint64_t* spare = bufB;
+    int64_t a = warp_add_coboundary<P>(c, s, stage, W, spare, 0, cap);
+    if (a < 0) { out_key = piv; out_status = ST_OVERFLOW; return; }
+    uint32_t adds = 0;
+    for (;;) {
+        if ((int)adds >= budget) { out_key = piv; out_status = ST_BUDGET; out_adds = adds; return; }
+        const int64_t na = warp_add_owner<P>(c, o, opos, stage, W, spare, a, cap);
+        if (na < 0) { out_key = piv; out_status = ST_OVERFLOW; out_adds = adds; return; }
+        ++adds;
+        a = na;
+        if (a == 0) { out_key = EMPTY; out_status = ST_COMPLETE; out_adds = adds; return; }
+        piv = W[0];
+        if (!warp_owner<P>(c, piv, self_key, o, opos)) {
+            out_key = piv;
+            out_status = ST_COMPLETE;
+            out_adds = adds;
+            store_reduced(c, j, W, a);
+            return;
+        }
+    }
+}
+
+__device__ void hash_insert(const Ctx& c, uint64_t key, uint32_t val) {
+    uint64_t sl = mix64(key) & c.hmask;
+    for (uint64_t probe = 0; probe <= c.hmask; ++probe) {
+        const unsigned long long prev =
+            atomicCAS(reinterpret_cast<unsigned long long*>(c.hkeys + sl), (unsigned long long)EMPTY,
+                      (unsigned long long)key);
+        if (prev == EMPTY || prev == key) { c.hvals[sl] = val; return; }
+        sl = (sl + 1) & c.hmask;
+    }
+    atomicExch(c.err, DEV_CAPACITY);
+}
+
+struct Emit {
+    PairRec* pairs;
+    unsigned long long* num_pairs;
+    uint32_t* clear_next;
+    unsigned long long* counters;  // [0] additions [1] pairs [2] essential
+    int keep_zero;
+};
+
+// Record the finished column j with pivot key `key` (EMPTY = zero column).
+__device__ void finish_column(const Ctx& c, const Emit& e, int64_t j, uint64_t key, uint32_t adds) {
+    const uint64_t ckey = c.cols[j];
+    const uint64_t cs = ckey & c.cmask;
+    const uint32_t rs = (uint32_t)((~(ckey >> c.cb)) & c.rmask);
+    PairRec pr;
+    pr.birth_rank = rs;
+    pr.birth_cidx = cs;
+    if (adds) atomicAdd(e.counters + 0, (unsigned long long)adds);
+    if (key == EMPTY) {  // zero column of an uncleared simplex: essential class
+        pr.death_rank = 0xFFFFFFFFu;
+        pr.death_cidx = -1;
+        atomicAdd(e.counters + 2, 1ull);
+        e.pairs[atomicAdd(e.num_pairs, 1ull)] = pr;
+        return;
+    }
+    const uint32_t rt = (uint32_t)(key >> c.rcb);
+    const uint64_t ct = c.rcmask - (key & c.rcmask);
+    hash_insert(c, ct, (uint32_t)j);
+    if (e.clear_next) atomicOr(e.clear_next + (ct >> 5), 1u << (ct & 31));
+    atomicAdd(e.counters + 1, 1ull);
+    if (rt > rs || e.keep_zero) {
+        pr.death_rank = rt;
+        pr.death_cidx = (int64_t)ct;
+        e.pairs[atomicAdd(e.num_pairs, 1ull)] = pr;
+    }
+}
+
+// One block: exclusive prefix-min of the pivot keys over U in order decides
+// which columns are final; the rest are compacted, in order, into Unext.
+// ---------------------------------------------------------------------------
+// Heavy columns: one 512-thread block per column, state kept across rounds.
+//
+// A column that needs many additions (the cocycle of a long bar can reach
+// hundreds of thousands of rows) is never merged as a whole.  Its rows are
+// split at a key Ks: the front F (rows < Ks, sorted, unique, at most FC of
+// them) lives in shared memory and is the only part the pivot search reads;
+// the back B (rows >= Ks) is an unsorted multiset in global memory to which
+// new rows are appended without sorting.  When F runs empty, a most-
+// significant-digit radix select over B finds a split T with at most FC/2
+// rows below it; those rows are sorted, rows of even multiplicity cancel
+// (Z/2), and the rest become the new front with Ks = T.  An addition thus
+// costs O(rows added + |F|), independent of the column's size.
+// ---------------------------------------------------------------------------
+constexpr int HT = 512;          // threads per block
+constexpr int HW = HT / 32;
+constexpr int FC = 4096;         // front capacity
+constexpr int FKEEP = FC - 1024; // front size kept after a spill
+constexpr int HSTAGE = 1024;     // rows generated or copied per pass (power of two >= HT)
+constexpr int REFILL = FC / 2;   // rows promoted from the back per refill (at most)
+
+struct HeavyState {
+    uint64_t* F;       // slots x FC, the front saved between rounds
+    uint64_t* B;       // slots x bcap
+    int64_t bcap;
+    uint64_t* Ks;      // per slot
+    int32_t* fsize;
+    int64_t* bsize;
+    uint8_t* init;     // 0: the column has not been started (or must restart)
+    uint32_t* adds;
+    unsigned long long* prof;  // VR_LOG only: cycles {refill, lookup, add, resume}, counts {adds, lookups}
+};
+
+struct HeavySmem {
+    uint64_t buf[2][FC];   // the front and its merge target, swapped after each merge
+    uint64_t stage[HSTAGE];
+    int ws[HW + 1];
+    uint32_t hist[256];
+    uint64_t Ks;
+    int64_t bsize;
+    int64_t opos;
+    int fsize;
+    int cur;               // which buf holds the front
+    int flag;
+    int ov[VR_MAX_DIM + 2];
+    uint32_t orank;
+    uint64_t sel;          // radix-select result
+};
+
+// exclusive block scan of one int per thread; *total receives the sum
+__device__ __forceinline__ int block_excl_scan(int x, int* ws, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < HW ? ws[lane] : 0;
+        int ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < HW) ws[lane] = ti - t;
+        if (lane == HW - 1) ws[HW] = ti;
+    }
+    __syncthreads();
+    const int r = ws[wid] + incl - x;
+    *total = ws[HW];
+    __syncthreads();
+    return r;
+}
+
+__device__ void block_bitonic(uint64_t* a, int len) {
+    for (int k = 2; k <= len; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < len; i += HT) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t x = a[i], y = a[ixj];
+                    if ((x > y) == ((i & k) == 0)) { a[i] = y; a[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Sort stage[0..cnt) ascending (pads to a power of two with EMPTY).
+__device__ void stage_sort(HeavySmem& S, int cnt) {
+    if (cnt <= 1) return;
+    int len = 2;
+    while (len < cnt) len <<= 1;
+    for (int i = cnt + threadIdx.x; i < len; i += HT) S.stage[i] = EMPTY;
+    __syncthreads();
+    block_bitonic(S.stage, len);
+}
+
+__device__ __forceinline__ int lower_bound_sm(const uint64_t* a, int len, uint64_t x) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Append rows to B; false (and nothing written) if B is full.
+__device__ bool heavy_append(HeavySmem& S, uint64_t* B, int64_t bcap, const uint64_t* src, int cnt) {
+    const int64_t bs = S.bsize;
+    if (bs + cnt > bcap) return false;
+    for (int i = threadIdx.x; i < cnt; i += HT) B[bs + i] = src[i];
+    __syncthreads();
+    if (threadIdx.x == 0) S.bsize = bs + cnt;
+    __syncthreads();
+    return true;
+}
+
+// front <- front XOR stage[0..b), stage sorted, unique and entirely below Ks.
+__device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
+    if (b == 0) return true;
+    const uint64_t* run = S.stage;
+    const uint64_t* F = S.buf[S.cur];
+    uint64_t* F2 = S.buf[S.cur ^ 1];
+    const int a = S.fsize;
+    // rows of F below run[0] keep their place
+    const int p0 = lower_bound_sm(F, a, run[0]);
+    for (int i = threadIdx.x; i < p0; i += HT) F2[i] = F[i];
+    const int rest = a - p0;
+    const int chunkF = (rest + HT - 1) / HT;
+    const int f0 = p0 + min(rest, (int)threadIdx.x * chunkF), f1 = min(a, f0 + chunkF);
+    int mloc = 0;
+    for (int i = f0; i < f1; ++i) {
+        int q = lower_bound_sm(run, b, F[i]);
+        mloc += (q < b && run[q] == F[i]);
+    }
+    int mtot;
+    int m = block_excl_scan(mloc, S.ws, &mtot);
+    for (int i = f0; i < f1; ++i) {
+        const uint64_t x = F[i];
+        const int q = lower_bound_sm(run, b, x);
+        if (q < b && run[q] == x) { ++m; continue; }
+        F2[i + q - 2 * m] = x;
+    }
+    const int chunkR = (b + HT - 1) / HT;
+    const int r0 = min(b, (int)threadIdx.x * chunkR), r1 = min(b, r0 + chunkR);
+    int mloc2 = 0;
+    for (int k = r0; k < r1; ++k) {
+        const int q = lower_bound_sm(F, a, run[k]);
+        mloc2 += (q < a && F[q] == run[k]);
+    }
+    int mt2;
+    int m2 = block_excl_scan(mloc2, S.ws, &mt2);
+    for (int k = r0; k < r1; ++k) {
+        const uint64_t y = run[k];
+        const int q = lower_bound_sm(F, a, y);
+        if (q < a && F[q] == y) { ++m2; continue; }
+        F2[k + q - 2 * m2] = y;
+    }
+    __syncthreads();
+    int na = a + b - 2 * mtot;
+    if (threadIdx.x == 0) S.cur ^= 1;
+    __syncthreads();
+    if (na > FKEEP) {  // spill the top of the front to B and lower the split
+        if (!heavy_append(S, B, bcap, S.buf[S.cur] + FKEEP, na - FKEEP)) return false;
+        if (threadIdx.x == 0) S.Ks = S.buf[S.cur][FKEEP];
+        na = FKEEP;
+    }
+    if (threadIdx.x == 0) S.fsize = na;
+    __syncthreads();
+    return true;
+}
+
+// W <- W + run for a sorted, unique run in stage[0..b) (any keys).
+__device__ bool heavy_add_run(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
+    const int lo = lower_bound_sm(S.stage, b, S.Ks);
+    if (!heavy_append(S, B, bcap, S.stage + lo, b - lo)) return false;
+    return heavy_merge_front(S, B, bcap, lo);
+}
+
+// Refill an empty front from B.  Returns false if the column is zero.
+__device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
+    for (;;) {
+        __syncthreads();
+        const int64_t bsz = S.bsize;
+        if (bsz == 0) return false;
+        // 1. split T with at most REFILL rows below it (MSD radix select)
+        uint64_t T = EMPTY;
+        if (bsz > REFILL) {
+            uint64_t prefix = 0;
+            int shift = ((keybits + 7) / 8) * 8 - 8;
+            if (shift < 0) shift = 0;
+            int64_t below = 0;
+            for (;;) {
+                for (int i = threadIdx.x; i < 256; i += HT) S.hist[i] = 0;
+                __syncthreads();
+                for (int64_t i = threadIdx.x; i < bsz; i += HT) {
+                    const uint64_t k = B[i];
+                    const bool in = shift + 8 >= 64 || (k >> (shift + 8)) == (prefix >> (shift + 8));
+                    if (in) atomicAdd(&S.hist[(k >> shift) & 0xFF], 1u);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int d = 0;
+                    int64_t bl = below;
+                    while (d < 256 && bl + S.hist[d] <= REFILL) bl += S.hist[d++];
+                    const uint64_t hi_mask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1);
+                    S.sel = (prefix & hi_mask) | ((uint64_t)d << shift);
+                    S.flag = bl > 0 ? 1 : (shift == 0 ? 2 : 0);  // 1 done, 2 one key, 0 descend
+                    S.ws[HW] = (int)bl;
+                }
+                __syncthreads();
+                const int fl = S.flag;
+                if (fl == 1) { T = S.sel; break; }
+                if (fl == 2) { T = S.sel + 1; break; }
+                prefix = S.sel;
+                below = S.ws[HW];
+                shift -= 8;
+                __syncthreads();
+            }
+        }
+        // 2. move rows < T to the spare buffer (tile by tile: B is compacted in place)
+        uint64_t* G = S.buf[S.cur ^ 1];
+        int nlt = 0;
+        int64_t nge = 0;
+        for (int64_t base = 0; base < bsz; base += HT) {
+            const int64_t i = base + threadIdx.x;
+            const uint64_t k = i < bsz ? B[i] : EMPTY;
+            const bool lt = i < bsz && k < T;
+            const bool ge = i < bsz && !lt;
+            int tot;
+            const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
+            if (lt && nlt + (packed & 0xFFFF) < FC) G[nlt + (packed & 0xFFFF)] = k;
+            if (ge) B[nge + (packed >> 16)] = k;
+            nlt += tot & 0xFFFF;
+            nge += tot >> 16;
+        }
+        __syncthreads();
+        if (nlt > FC) {  // a single key with more copies than fit: keep its parity only
+            if (threadIdx.x == 0) {
+                S.buf[S.cur][0] = T - 1;
+                S.fsize = (nlt & 1) ? 1 : 0;
+                S.bsize = nge;
+                S.Ks = T;
+            }
+            __syncthreads();
+            if (S.fsize) return true;
+            continue;
+        }
+        int len = 1;
+        while (len < nlt) len <<= 1;
+        for (int i = nlt + threadIdx.x; i < len; i += HT) G[i] = EMPTY;
+        __syncthreads();
+        block_bitonic(G, len);
+        // 3. keep the rows of odd multiplicity
+        uint64_t* F = S.buf[S.cur];
+        const int chunk = (nlt + HT - 1) / HT;
+        const int c0 = min(nlt, (int)threadIdx.x * chunk), c1 = min(nlt, c0 + chunk);
+        int keep = 0;
+        for (int i = c0; i < c1; ++i) {
+            if (i > 0 && G[i - 1] == G[i]) continue;
+            int e = i;
+            while (e + 1 < nlt && G[e + 1] == G[i]) ++e;
+            keep += ((e - i + 1) & 1);
+        }
+        int tk;
+        int pos = block_excl_scan(keep, S.ws, &tk);
+        for (int i = c0; i < c1; ++i) {
+            if (i > 0 && G[i - 1] == G[i]) continue;
+            int e = i;
+            while (e + 1 < nlt && G[e + 1] == G[i]) ++e;
+            if ((e - i + 1) & 1) F[pos++] = G[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S.fsize = tk;
+            S.bsize = nge;
+            S.Ks = T;
+        }
+        __syncthreads();
+        if (tk > 0) return true;
+    }
+}
+
+// W <- W + D_x for the p-simplex x (vertices ascending, diameter rank xr):
+// rows at or above the split go straight to B, only the few below it are
+// sorted and merged into the front.
+template <int P>
+__device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x) {
+    const int64_t n = c.R.n;
+    for (int64_t base = n - 1; base >= 0; base -= HT) {
+        const int64_t w = base - (int64_t)threadIdx.x;
+        bool ok = w >= 0;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
+        uint32_t rt = x.r;
+        uint64_t key = EMPTY;
+        if (ok) {
+#pragma unroll
+            for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
+            ok = rt <= c.thr;
+            if (ok) key = row_key<P>(c, x, w, rt);
+        }
+        const bool lt = ok && key < S.Ks;
+        const bool ge = ok && !lt;
+        int tot;
+        const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
+        const int nlt = tot & 0xFFFF, nge = tot >> 16;
+        const int64_t bs = S.bsize;
+        if (bs + nge > bcap) return false;
+        if (ge) B[bs + (packed >> 16)] = key;
+        if (lt) S.stage[packed & 0xFFFF] = key;
+        __syncthreads();
+        if (threadIdx.x == 0) S.bsize = bs + nge;
+        __syncthreads();
+        stage_sort(S, nlt);
+        if (!heavy_merge_front(S, B, bcap, nlt)) return false;
+    }
+    return true;
+}
+
+// W <- W + R_o where R_o is a stored reduced column (sorted, unique).
+__device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, int64_t opos) {
+    const uint64_t* run = c.pool + c.rc_off[opos];
+    const int64_t len = c.rc_len[opos];
+    for (int64_t base = 0; base < len; base += HSTAGE) {
+        const int cnt = (int)min((int64_t)HSTAGE, len - base);
+        for (int i = threadIdx.x; i < cnt; i += HT) S.stage[i] = run[base + i];
+        __syncthreads();
+        if (!heavy_add_run(S, B, bcap, cnt)) return false;
+    }
+    return true;
+}
+
+// Owner of pivot rk (see warp_owner); result in S.opos / S.ov / S.orank.
+template <int P>
+__device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t self_key) {
+    constexpr int NT = P + 2;
+    constexpr int NPAIR = NT * (NT - 1) / 2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n = c.R.n;
+    const uint32_t rt = (uint32_t)(rk >> c.rcb);
+    const uint64_t ct = c.rcmask - (rk & c.rcmask);
+    if (wid == 0) {
+        int64_t pos = warp_hash_find(c, ct);
+        int flag = 0;  // 1 = stored column owner, 2 = candidate apparent owner, 0 = none
+        int drop = -1;
+        int tv[NT];
+        if (pos >= 0) {
+            flag = 1;
+        } else {
+            decode_simplex<P + 1>(c.B, ct, n - 1, tv);
+            bool eq = false;
+            int pi = 0, pj = 0;
+            if (lane < NPAIR) {
+                int k = lane;
+                pi = 1;
+                while (k >= pi) { k -= pi; ++pi; }
+                pj = k;
+                eq = c.R(tv[pi], tv[pj]) == rt;
+            }
+#pragma unroll
+            for (int m = NT - 1; m >= 0; --m)
+                if (drop < 0 && __ballot_sync(0xffffffffu, eq && pi != m && pj != m)) drop = m;
+            if (drop >= 0) flag = 2;
+        }
+        if (lane == 0) {
+            S.flag = flag;
+            S.opos = pos;
+            if (flag == 2) {
+                int k = 0;
+                for (int q = 0; q < NT; ++q)
+                    if (q != drop) S.ov[k++] = tv[q];
+                S.ov[P + 1] = tv[drop];  // the dropped vertex
+                S.orank = rt;
+            }
+        }
+    }
+    __syncthreads();
+    const int flag = S.flag;
+    if (flag == 0) return false;
+    if (flag == 1) {
+        if (threadIdx.x == 0) {
+            const uint64_t okey = c.cols[S.opos];
+            if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL);
+        }
+        return true;
+    }
+    // apparent iff no vertex w above the dropped one keeps the diameter of s'
+    int ov[P + 1];
+#pragma unroll
+    for (int q = 0; q <= P; ++q) ov[q] = S.ov[q];
+    const int64_t wd = S.ov[P + 1];
+    bool older = false;
+    for (int64_t base = n - 1; base > wd; base -= HT) {
+        const int64_t w = base - (int64_t)threadIdx.x;
+        bool ok = w > wd;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (w != ov[q]);
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (c.R(ov[q], w) <= rt);
+        older = older || ok;
+    }
+    return !__syncthreads_or(older);
+}
+
+
+}  // namespace
+}  // namespace vr

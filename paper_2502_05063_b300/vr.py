@@ -173,6 +173,49 @@ def barcodes(points=None, dists=None, n=None, dmax=1, threshold=np.inf, flags=0,
         lib.vr_result_free(out)
 
 
+class BatchBarcodes:
+    """Pairs of many clouds: pairs[p] (structured array of all clouds, cloud i at
+    offsets[p][i]:offsets[p][i+1]), critical_edges[p] or None, thresholds[i]."""
+
+    def __init__(self, res: BatchResult):
+        self.num_clouds, self.dmax = res.num_clouds, res.dmax
+        self.pairs, self.offsets, self.critical_edges = [], [], []
+        nc = res.num_clouds
+        self.thresholds = np.ctypeslib.as_array(res.thresholds, shape=(max(nc, 1),))[:nc].copy()
+        for p in range(res.dmax + 1):
+            off = np.ctypeslib.as_array(res.pair_offsets[p], shape=(nc + 1,)).copy()
+            m = int(off[-1])
+            if m:
+                buf = ctypes.cast(res.pairs[p], ctypes.POINTER(ctypes.c_char * (m * PAIR_DTYPE.itemsize))).contents
+                arr = np.frombuffer(bytes(buf), dtype=PAIR_DTYPE).copy()
+            else:
+                arr = np.zeros(0, dtype=PAIR_DTYPE)
+            edges = None
+            if res.critical_edges[p]:
+                edges = np.ctypeslib.as_array(res.critical_edges[p], shape=(max(m, 1) * 4,))[: 4 * m].reshape(m, 4).copy()
+            self.pairs.append(arr)
+            self.offsets.append(off)
+            self.critical_edges.append(edges)
+
+    def cloud(self, i, p):
+        return self.pairs[p][self.offsets[p][i]:self.offsets[p][i + 1]]
+
+
+def barcodes_batched(points, offsets, dmax=1, threshold=np.inf, flags=0, stream=None) -> BatchBarcodes:
+    """Barcodes of clouds stored back to back in `points` (float32 (sum n, D),
+    numpy or torch, host or GPU); offsets: int64 (num+1,) host array."""
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    ptr, keep = _ptr_of(points)
+    out = ctypes.POINTER(BatchResult)()
+    code = lib.vr_barcodes_batched(ptr, offs.ctypes.data, len(offs) - 1, int(points.shape[1]), int(dmax),
+                                   float(threshold), int(flags), _stream_ptr(stream), ctypes.byref(out))
+    _check(code, "vr_barcodes_batched")
+    try:
+        return BatchBarcodes(out.contents)
+    finally:
+        lib.vr_batch_result_free(out)
+
+
 def simplex_vertices(cidx: int, q: int, n: int):
     v = np.zeros(q + 1, dtype=np.int32)
     _check(lib.vr_simplex_vertices(int(cidx), int(q), int(n), v.ctypes.data), "vr_simplex_vertices")

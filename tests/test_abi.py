@@ -1,0 +1,78 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/vr.h, and rejects bad arguments before touching CUDA.
+Host-only arithmetic (the simplex index map of eq. 5.6) is compared with the
+oracle."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def vr():
+    from paper_2502_05063_b300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_2502_05063_b300 import vr as _vr
+    return _vr
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "vr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:vr_status|void|const char\s*\*)\s+(vr_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(vr):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(vr.lib, name), name
+
+
+def test_status_strings(vr):
+    for code, name in vr.STATUS.items():
+        s = vr.lib.vr_status_string(code).decode()
+        assert s and s != "unknown status", name
+
+
+def test_simplex_vertices_matches_oracle(vr):
+    rng = np.random.default_rng(0)
+    for q in range(0, 5):
+        n = int(rng.integers(q + 1, 60))
+        total = math.comb(n, q + 1)
+        for c in set(rng.integers(0, total, size=20).tolist()) | {0, total - 1}:
+            assert vr.simplex_vertices(c, q, n) == oracle.simplex_vertices(c, q, n)
+    with pytest.raises(vr.VRError):
+        vr.simplex_vertices(math.comb(10, 3), 2, 10)  # out of range
+
+
+def test_argument_checks_before_cuda(vr):
+    out = ctypes.POINTER(vr.Result)()
+    pts = np.zeros((4, 3), np.float32)
+    p = pts.ctypes.data
+    assert vr.lib.vr_barcodes_points(p, 0, 3, 1, float("inf"), 0, None, ctypes.byref(out)) == 1
+    assert vr.lib.vr_barcodes_points(p, 4, 3, 7, float("inf"), 0, None, ctypes.byref(out)) == 1
+    assert vr.lib.vr_barcodes_points(p, 4, 0, 1, float("inf"), 0, None, ctypes.byref(out)) == 1
+    assert vr.lib.vr_barcodes_points(p, 4, 3, 1, float("nan"), 0, None, ctypes.byref(out)) == 1
+    assert vr.lib.vr_barcodes_points(p, 4, 3, 1, 1.0, 0x80, None, ctypes.byref(out)) == 1
+    assert not out
+    assert vr.lib.vr_sort_u64_noalloc(None, None, vr.VR_SORT_NOALLOC_MAX_KEYS + 1, 64, None) == 1
+    assert vr.lib.vr_sort_u64(None, None, -1, 64, None) == 1
+    assert vr.lib.vr_backward(None, 0, 3, None, 0, None, None, None, None) == 1
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The library and its binding never load the oracle."""
+    src = open(os.path.join(ROOT, "paper_2502_05063_b300", "vr.py")).read()
+    assert "oracle" not in src.split('"""', 2)[2]
+    for f in os.listdir(os.path.join(ROOT, "paper_2502_05063_b300", "csrc")):
+        text = open(os.path.join(ROOT, "paper_2502_05063_b300", "csrc", f)).read()
+        assert "vr_oracle" not in text and "or_cohom" not in text

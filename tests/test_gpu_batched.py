@@ -1,0 +1,96 @@
+"""The batched form (one persistent launch over many clouds) against the
+single-cloud path and against the oracle.  Bit-exact, like every parity test."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_05063_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for the gpu tests")
+    from paper_2502_05063_b300 import vr as _vr
+    return _vr
+
+
+def rows(a):
+    return [(float(r["birth"]), float(r["death"]), int(r["birth_simplex"]), int(r["death_simplex"])) for r in a]
+
+
+def mixed_clouds(num, seed, nmax=256):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(num):
+        n = int(rng.integers(1, nmax + 1)) if i % 5 else int(rng.integers(1, 6))
+        kind = i % 4
+        if kind == 0:
+            x = synth.circle(n, float(rng.uniform(0.5, 2)), 0.05, 3, g=rng)
+        elif kind == 1:
+            x = synth.sphere(n, 3, float(rng.uniform(0.5, 2)), 0.05, g=rng)
+        elif kind == 2:
+            x = rng.random((n, 3)).astype(np.float32)
+        else:
+            x = rng.integers(0, 3, size=(n, 3)).astype(np.float32)  # ties and duplicates
+        out.append(x)
+    return out
+
+
+@pytest.mark.parametrize("dmax,thr,flags", [(1, np.inf, 0), (1, 0.8, 2), (0, np.inf, 0)])
+def test_batched_equals_single(vr, dmax, thr, flags):
+    clouds = mixed_clouds(60, seed=dmax * 10 + int(np.isfinite(thr)))
+    pts, offs = synth.pack(clouds)
+    bb = vr.barcodes_batched(pts, offs, dmax=dmax, threshold=thr, flags=flags)
+    for i, c in enumerate(clouds):
+        single = vr.barcodes(points=c, dmax=dmax, threshold=thr, flags=flags)
+        for p in range(dmax + 1):
+            assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
+            if flags & vr.VR_CRITICAL_EDGES:
+                e = bb.critical_edges[p][bb.offsets[p][i]:bb.offsets[p][i + 1]]
+                assert e.tolist() == single.critical_edges[p].tolist(), (i, p)
+        assert bb.thresholds[i] == np.float32(single.threshold)
+
+
+def test_batch4096_workload(vr):
+    """The full 4096-cloud workload: every cloud equals the single-cloud path,
+    every 64th cloud equals the oracle."""
+    import torch
+    clouds, kinds = synth.batch_clouds()
+    pts, offs = synth.pack(clouds)
+    bb = vr.barcodes_batched(torch.from_numpy(pts).cuda(), offs, dmax=1)
+    for i in range(0, len(clouds), 64):
+        c = clouds[i]
+        n = c.shape[0]
+        D = oracle.distances_f32(c).astype(np.float64)
+        pairs, _ = oracle.cohom(D, n, 1, oracle.enclosing_radius(D, n), clearing=True)
+        dg = oracle.diagram(pairs, 1)
+        for p in range(2):
+            want = [(float(np.float32(r["birth"])), float(np.float32(r["death"])) if np.isfinite(r["death"]) else math.inf,
+                     int(r["birth_cidx"]), int(r["death_cidx"])) for r in dg[p]]
+            assert rows(bb.cloud(i, p)) == want, (i, p, kinds[i])
+    for i in range(1, len(clouds), 7):
+        single = vr.barcodes(points=clouds[i], dmax=1)
+        for p in range(2):
+            assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
+
+
+def test_batched_repeat_and_shapes(vr):
+    clouds = mixed_clouds(10, seed=5)
+    pts, offs = synth.pack(clouds)
+    a = vr.barcodes_batched(pts, offs, dmax=1)
+    b = vr.barcodes_batched(pts, offs, dmax=1)  # graph replay
+    for p in range(2):
+        assert rows(a.pairs[p]) == rows(b.pairs[p])
+    c = vr.barcodes_batched(pts[: offs[3]], offs[:4], dmax=1)  # another shape
+    for i in range(3):
+        for p in range(2):
+            assert rows(c.cloud(i, p)) == rows(a.cloud(i, p))
+    with pytest.raises(vr.VRError):
+        big = np.zeros((300, 3), np.float32)
+        vr.barcodes_batched(big, np.array([0, 300]), dmax=1)
