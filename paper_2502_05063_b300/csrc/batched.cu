@@ -42,9 +42,11 @@ constexpr int BMAXDIM = 16;
 constexpr int BLD = BMAXN;             // row stride of a cloud's square matrix
 constexpr int CCAP = 8192;             // non-apparent columns per cloud
 constexpr int HCAP = 16384;            // hash slots per cloud (power of two, >= 2 CCAP)
-constexpr int64_t BACKCAP = 1 << 17;   // back rows of the block engine per cloud
+constexpr int64_t BACKCAP = 1 << 20;   // back rows of the block engine per cloud (8 MB)
 constexpr int EDGE_BITS = 15;          // C(256,2) - 1 < 2^15
 constexpr int TRI_BITS = 22;           // C(256,3) - 1 < 2^22
+constexpr int WCAP = 2048;             // per-warp working column of the first pass
+constexpr int64_t POOLCAP = 1 << 15;   // stored reduced columns per cloud
 
 struct BatchArgs {
     const float* pts;
@@ -66,6 +68,13 @@ struct BatchArgs {
     uint32_t* ulist;
     PairRec* h1tmp;
     uint64_t* back;
+    uint64_t* wstage;      // slots x HW x STAGE
+    uint64_t* wbuf;        // slots x HW x 2 x WCAP
+    uint64_t* pool;        // slots x POOLCAP
+    unsigned long long* pool_used;  // per slot
+    uint64_t* rc_off;      // slots x CCAP
+    uint32_t* rc_len;      // slots x CCAP
+    uint32_t* adds;        // slots x CCAP
     const uint64_t* binom;  // C(v,k), v <= 256, k <= 3
     // outputs (per dimension p = 0, 1)
     PairRec* recs[2];
@@ -78,6 +87,7 @@ struct BatchArgs {
     int32_t* cloud_err;
     unsigned long long* work;
     unsigned long long* stats;  // [0] candidates [1] apparent [2] columns [3] additions
+    unsigned long long* prof;   // VR_LOG only: cycles per phase, summed over clouds (thread 0 of each block)
 };
 
 struct BatchSmem {
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
     uint64_t* cols = A.cols + slot * (int64_t)CCAP;
     uint64_t* cur_key = A.cur_key + slot * (int64_t)CCAP;
     uint8_t* status = A.status + slot * (int64_t)CCAP;
-    uint32_t* ulist = A.ulist + slot * (int64_t)CCAP;
+    uint32_t* ulist = A.ulist + slot * (int64_t)(2 * CCAP);
     PairRec* h1tmp = A.h1tmp + slot * (int64_t)CCAP;
     uint64_t* back = A.back + slot * BACKCAP;
     const Binom B{A.binom, BMAXN, 3};
@@ -198,6 +208,16 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
         const int n = (int)(A.offs[cloud + 1] - o0);
         const int ne = n * (n - 1) / 2;
         if (threadIdx.x == 0) { M.h0n = 0; M.ncols = 0; M.nh1 = 0; M.nu = 0; M.overflow = 0; }
+        long long tp = clock64();
+        const long long t_cloud = tp;
+#define VR_PHASE(i)                                                          \
+    do {                                                                     \
+        if (A.prof && threadIdx.x == 0) {                                    \
+            const long long t_ = clock64();                                  \
+            atomicAdd(A.prof + (i), (unsigned long long)(t_ - tp));          \
+            tp = t_;                                                         \
+        }                                                                    \
+    } while (0)
         // ---- 1. points and distances (bits of the single-precision formula)
         for (int i = threadIdx.x; i < n * A.dim; i += HT) M.pts[i] = A.pts[o0 * A.dim + i];
         for (int i = threadIdx.x; i < (ne + 31) / 32; i += HT) M.clear[i] = 0;
@@ -233,6 +253,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
         }
         const uint32_t thr = M.thr;
         if (threadIdx.x == 0) A.thr_used[cloud] = __uint_as_float(thr);
+        VR_PHASE(0);
         // ---- 3a. warp 0: spanning tree and elder rule
         if (wid == 0) {
             uint64_t best[BMAXN / 32];
@@ -357,6 +378,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             if (lane == 0 && c_cand) atomicAdd(A.stats + 0, c_cand);
         }
         __syncthreads();
+        VR_PHASE(1);
         if (M.overflow) {
             if (threadIdx.x == 0) A.cloud_err[cloud] = 1;
             __syncthreads();
@@ -374,6 +396,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             if (len <= BMAXN) block_sort_recs(M.h0, len);
             emit_block(A, M, 0, cloud, M.h0, h, R, B);
         }
+        VR_PHASE(2);
         if (A.dmax < 1) continue;
         // ---- 4. drop cleared columns, sort the rest into coboundary order
         int m = M.ncols;
@@ -397,6 +420,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             block_bitonic(cols, len);
             if (threadIdx.x == 0) atomicAdd(A.stats + 2, (unsigned long long)m);
         }
+        VR_PHASE(3);
         // ---- 5. reduction
         Ctx c;
         c.R = R;
@@ -415,81 +439,107 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
         while (hsz < 2 * (uint64_t)m) hsz <<= 1;
         c.hmask = hsz - 1;
         c.err = A.cloud_err + cloud;
-        c.pool = nullptr; c.pool_used = nullptr; c.pool_cap = 0; c.rc_off = nullptr; c.rc_len = nullptr;
+        c.pool = A.pool + slot * POOLCAP;
+        c.pool_used = A.pool_used + slot;
+        c.pool_cap = POOLCAP;
+        c.rc_off = A.rc_off + slot * (int64_t)CCAP;
+        c.rc_len = A.rc_len + slot * (int64_t)CCAP;
+        uint32_t* adds_j = A.adds + slot * (int64_t)CCAP;
         for (uint64_t i = threadIdx.x; i < hsz; i += HT) c.hkeys[i] = EMPTY;
+        if (threadIdx.x == 0) *c.pool_used = 0;
         __syncthreads();
-        // 5a. every column once, no additions
-        for (int j = wid; j < m; j += HW) {
-            Simplex<1> s, o;
-            int64_t opos;
-            load_col<1>(c, cols[j], s);
-            const uint64_t piv = warp_column_pivot<1>(c, s);
-            uint8_t st = ST_COMPLETE;
-            if (piv != EMPTY && warp_owner<1>(c, piv, cols[j], o, opos)) st = ST_BUDGET;
-            if (lane == 0) { cur_key[j] = piv; status[j] = st; }
-        }
+        // 5a/5b. rounds over the unfinished columns: one warp each with a budget
+        // of additions that doubles per round, then finalization in order by the
+        // prefix-minimum rule; stop when all are final or a round makes no progress
+        uint32_t* ucur = ulist;
+        uint32_t* unext = ulist + CCAP;
+        for (int i = threadIdx.x; i < m; i += HT) ucur[i] = (uint32_t)i;
+        int nu = m;
+        int budget = 8;
         __syncthreads();
-        // 5b. finalize in order by the prefix-minimum rule; the rest goes to ulist
-        if (threadIdx.x == 0) { M.carry_min = EMPTY; M.carry_cnt = 0; }
-        __syncthreads();
-        for (int base = 0; base < m; base += HT) {
-            const int j = base + threadIdx.x;
-            const bool valid = j < m;
-            const uint64_t key = valid ? cur_key[j] : EMPTY;
-            const uint8_t st = valid ? status[j] : ST_COMPLETE;
-            uint64_t incl = key;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o && y < incl) incl = y;
-            }
-            if (lane == 31) M.wmin[wid] = incl;
-            __syncthreads();
-            uint64_t pm = M.carry_min;
-            for (int w = 0; w < wid; ++w) pm = min(pm, M.wmin[w]);
-            uint64_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
-            if (lane > 0) pm = min(pm, excl);
-            const bool fin = valid && st == ST_COMPLETE && (key == EMPTY || key < pm);
-            const bool keep = valid && !fin;
-            if (fin) {
-                const uint64_t ck = cols[j];
-                PairRec pr;
-                pr.birth_rank = (uint32_t)(~(ck >> EDGE_BITS));
-                pr.birth_cidx = ck & c.cmask;
-                bool out = true;
-                if (key == EMPTY) {
-                    pr.death_rank = 0xFFFFFFFFu; pr.death_cidx = -1;
-                } else {
-                    pr.death_rank = (uint32_t)(key >> TRI_BITS);
-                    pr.death_cidx = (int64_t)(c.rcmask - (key & c.rcmask));
-                    hash_insert(c, (uint64_t)pr.death_cidx, (uint32_t)j);
-                    out = pr.death_rank > pr.birth_rank;
+        while (nu > 0) {
+            {
+                uint64_t* wst = A.wstage + (slot * HW + wid) * (int64_t)STAGE;
+                uint64_t* wa = A.wbuf + (slot * HW + wid) * (int64_t)(2 * WCAP);
+                for (int q = wid; q < nu; q += HW) {
+                    const int j = ucur[q];
+                    uint64_t key;
+                    uint8_t st;
+                    uint32_t ad;
+                    reduce_one<1>(c, j, budget, wst, wa, wa + WCAP, WCAP, key, st, ad);
+                    if (lane == 0) { cur_key[j] = key; status[j] = st; adds_j[j] = ad; }
                 }
-                if (out) h1tmp[atomicAdd(&M.nh1, 1)] = pr;
-            }
-            const uint32_t kb = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) M.wcnt[wid] = __popc(kb);
-            __syncthreads();
-            int before = 0, total = 0;
-            for (int w = 0; w < HW; ++w) {
-                if (w < wid) before += M.wcnt[w];
-                total += M.wcnt[w];
-            }
-            if (keep) ulist[M.carry_cnt + before + __popc(kb & ((1u << lane) - 1u))] = (uint32_t)j;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint64_t cm = M.carry_min;
-                for (int w = 0; w < HW; ++w) cm = min(cm, M.wmin[w]);
-                M.carry_min = cm;
-                M.carry_cnt += total;
             }
             __syncthreads();
+            if (threadIdx.x == 0) { M.carry_min = EMPTY; M.carry_cnt = 0; }
+            __syncthreads();
+            for (int base = 0; base < nu; base += HT) {
+                const bool valid = base + (int)threadIdx.x < nu;
+                const int j = valid ? (int)ucur[base + threadIdx.x] : 0;
+                const uint64_t key = valid ? cur_key[j] : EMPTY;
+                const uint8_t st = valid ? status[j] : ST_COMPLETE;
+                uint64_t incl = key;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o && y < incl) incl = y;
+                }
+                if (lane == 31) M.wmin[wid] = incl;
+                __syncthreads();
+                uint64_t pm = M.carry_min;
+                for (int w = 0; w < wid; ++w) pm = min(pm, M.wmin[w]);
+                const uint64_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+                if (lane > 0) pm = min(pm, excl);
+                const bool fin = valid && st == ST_COMPLETE && (key == EMPTY || key < pm);
+                const bool keep = valid && !fin;
+                if (fin) {
+                    if (adds_j[j]) atomicAdd(A.stats + 3, (unsigned long long)adds_j[j]);
+                    const uint64_t ck = cols[j];
+                    PairRec pr;
+                    pr.birth_rank = (uint32_t)(~(ck >> EDGE_BITS));
+                    pr.birth_cidx = ck & c.cmask;
+                    bool out = true;
+                    if (key == EMPTY) {
+                        pr.death_rank = 0xFFFFFFFFu; pr.death_cidx = -1;
+                    } else {
+                        pr.death_rank = (uint32_t)(key >> TRI_BITS);
+                        pr.death_cidx = (int64_t)(c.rcmask - (key & c.rcmask));
+                        hash_insert(c, (uint64_t)pr.death_cidx, (uint32_t)j);
+                        out = pr.death_rank > pr.birth_rank;
+                    }
+                    if (out) h1tmp[atomicAdd(&M.nh1, 1)] = pr;
+                }
+                const uint32_t kb = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) M.wcnt[wid] = __popc(kb);
+                __syncthreads();
+                int before = 0, total = 0;
+                for (int w = 0; w < HW; ++w) {
+                    if (w < wid) before += M.wcnt[w];
+                    total += M.wcnt[w];
+                }
+                if (keep) unext[M.carry_cnt + before + __popc(kb & ((1u << lane) - 1u))] = (uint32_t)j;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    uint64_t cm = M.carry_min;
+                    for (int w = 0; w < HW; ++w) cm = min(cm, M.wmin[w]);
+                    M.carry_min = cm;
+                    M.carry_cnt += total;
+                }
+                __syncthreads();
+            }
+            const int nn = M.carry_cnt;
+            uint32_t* t = ucur; ucur = unext; unext = t;
+            const bool stalled = nn == nu;
+            nu = nn;
+            if (stalled) break;
+            if (budget < (1 << 20)) budget *= 2;
         }
+        VR_PHASE(5);
         // 5c. the remaining columns in order, each to completion (block engine)
-        const int nu = M.carry_cnt;
+        if (A.prof && threadIdx.x == 0) atomicAdd(A.prof + 8, (unsigned long long)nu);
         unsigned long long adds = 0;
         for (int q = 0; q < nu; ++q) {
-            const int j = ulist[q];
+            const int j = ucur[q];
             const uint64_t self_key = cols[j];
             Simplex<1> s;
             load_col<1>(c, self_key, s);
@@ -502,13 +552,17 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
                 key = S.buf[S.cur][0];
                 if (!heavy_owner<1>(c, S, key, self_key)) break;
                 Simplex<1> o;
-                if (S.flag == 1) {
-                    load_col<1>(c, cols[S.opos], o);
+                if (S.flag == 1 && c.rc_len[S.opos]) {
+                    ok = heavy_add_stored(c, S, back, BACKCAP, S.opos);
                 } else {
-                    o.v[0] = S.ov[0]; o.v[1] = S.ov[1];
-                    o.r = S.orank;
+                    if (S.flag == 1) {
+                        load_col<1>(c, cols[S.opos], o);
+                    } else {
+                        o.v[0] = S.ov[0]; o.v[1] = S.ov[1];
+                        o.r = S.orank;
+                    }
+                    ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, o);
                 }
-                ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, o);
                 ++adds;
                 __syncthreads();
             }
@@ -535,6 +589,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             __syncthreads();
         }
         if (threadIdx.x == 0 && adds) atomicAdd(A.stats + 3, adds);
+        VR_PHASE(6);
         if (M.overflow) {
             if (threadIdx.x == 0) A.cloud_err[cloud] = 1;
             __syncthreads();
@@ -552,7 +607,10 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             block_sort_recs(h1tmp, len);
             emit_block(A, M, 1, cloud, h1tmp, h, R, B);
         }
+        VR_PHASE(7);
+        if (A.prof && threadIdx.x == 0) A.prof[16 + cloud] = (unsigned long long)(clock64() - t_cloud);
     }
+#undef VR_PHASE
 }
 
 // Ordered copy of the appended records: cloud i's pairs of dimension p go to
@@ -634,8 +692,9 @@ BatchPlan* g_plan = nullptr;
 std::map<std::pair<int, int64_t>, int> g_tuned;  // (device, mean-size bucket) -> slots per SM
 
 size_t slot_bytes() {
-    return (size_t)BMAXN * BLD * 4 + (size_t)HCAP * 12 + (size_t)CCAP * (8 + 8 + 1 + 4 + sizeof(PairRec)) +
-           (size_t)BACKCAP * 8 + 4096;
+    return (size_t)BMAXN * BLD * 4 + (size_t)HCAP * 12 +
+           (size_t)CCAP * (8 + 8 + 1 + 8 + sizeof(PairRec) + 8 + 4 + 4) + (size_t)BACKCAP * 8 +
+           (size_t)HW * STAGE * 8 + (size_t)HW * 2 * WCAP * 8 + (size_t)POOLCAP * 8 + 16 * 256;
 }
 
 void free_plan(BatchPlan* p) {
@@ -690,11 +749,20 @@ BatchPlan* make_plan(int dev, int num, int dim, int dmax, int want_edges, int th
         A.cols = carve<uint64_t>(cur, (size_t)slots * CCAP);
         A.cur_key = carve<uint64_t>(cur, (size_t)slots * CCAP);
         A.status = carve<uint8_t>(cur, (size_t)slots * CCAP);
-        A.ulist = carve<uint32_t>(cur, (size_t)slots * CCAP);
+        A.ulist = carve<uint32_t>(cur, (size_t)slots * 2 * CCAP);
         A.h1tmp = carve<PairRec>(cur, (size_t)slots * CCAP);
         A.back = carve<uint64_t>(cur, (size_t)slots * BACKCAP);
+        A.wstage = carve<uint64_t>(cur, (size_t)slots * HW * STAGE);
+        A.wbuf = carve<uint64_t>(cur, (size_t)slots * HW * 2 * WCAP);
+        A.pool = carve<uint64_t>(cur, (size_t)slots * POOLCAP);
+        A.pool_used = carve<unsigned long long>(cur, (size_t)slots);
+        A.rc_off = carve<uint64_t>(cur, (size_t)slots * CCAP);
+        A.rc_len = carve<uint32_t>(cur, (size_t)slots * CCAP);
+        A.adds = carve<uint32_t>(cur, (size_t)slots * CCAP);
         uint64_t* binom = carve<uint64_t>(cur, (size_t)4 * (BMAXN + 1));
         A.work = carve<unsigned long long>(cur, 8);
+        A.prof = log_enabled() ? carve<unsigned long long>(cur, 16 + (size_t)num) : nullptr;
+        if (A.prof) VR_CUDA(cudaMemset(A.prof, 0, (16 + (size_t)num) * sizeof(unsigned long long)));
         A.used = A.work + 1;
         A.stats = A.work + 3;
         std::vector<uint64_t> hb = host_binomials(BMAXN, 3);
@@ -864,6 +932,26 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
                                     cudaMemcpyDeviceToHost, s));
             VR_CUDA(cudaStreamSynchronize(s));
         }
+        if (P->args.prof) {
+            unsigned long long pr[16], st[4];
+            VR_CUDA(cudaMemcpy(pr, P->args.prof, sizeof pr, cudaMemcpyDeviceToHost));
+            VR_CUDA(cudaMemcpy(st, P->args.stats, sizeof st, cudaMemcpyDeviceToHost));
+            const char* names[8] = {"distances+threshold", "H0 tree + apparent", "H0 output", "clear+sort",
+                                    "first pass", "finalize", "block engine", "H1 output"};
+            for (int i = 0; i < 8; ++i) fprintf(stderr, "[vr] batch %-20s %14llu cycles (all clouds, cumulative)\n", names[i], pr[i]);
+            fprintf(stderr, "[vr] batch: candidates %llu apparent %llu columns %llu additions %llu, block-engine columns %llu\n",
+                    st[0], st[1], st[2], st[3], pr[8]);
+            std::vector<unsigned long long> pc(num_clouds);
+            VR_CUDA(cudaMemcpy(pc.data(), P->args.prof + 16, num_clouds * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost));
+            std::vector<int> ix(num_clouds);
+            for (int i = 0; i < num_clouds; ++i) ix[i] = i;
+            std::sort(ix.begin(), ix.end(), [&](int a, int b) { return pc[a] > pc[b]; });
+            for (int t = 0; t < std::min(num_clouds, 8); ++t)
+                fprintf(stderr, "[vr] batch slowest cloud %d: n=%lld, %llu cycles\n", ix[t],
+                        (long long)(offsets[ix[t] + 1] - offsets[ix[t]]), pc[ix[t]]);
+            VR_CUDA(cudaMemset(P->args.prof, 0, 16 * sizeof(unsigned long long)));
+        }
         // results in cloud order
         VR_CUDA(cudaMemcpyAsync(res->thresholds, P->args.thr_used, num_clouds * sizeof(float), cudaMemcpyDeviceToHost, s));
         for (int p = 0; p <= dmax; ++p)
@@ -871,8 +959,12 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
                                     cudaMemcpyDeviceToHost, s));
         VR_CUDA(cudaStreamSynchronize(s));
         std::vector<int> bad;
+        int codes[8] = {0};
         for (int i = 0; i < num_clouds; ++i)
-            if (cerr[i]) bad.push_back(i);
+            if (cerr[i]) { bad.push_back(i); codes[cerr[i] & 7]++; }
+        if (log_enabled() && !bad.empty())
+            fprintf(stderr, "[vr] batch: %zu clouds recomputed singly (codes 1:%d 2:%d 3:%d 4:%d)\n", bad.size(),
+                    codes[1], codes[2], codes[3], codes[4]);
         // clouds that outgrew a per-block buffer: recompute with the single-cloud path
         std::vector<vr_result*> redo(bad.size(), nullptr);
         for (size_t b = 0; b < bad.size(); ++b) {
