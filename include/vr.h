@@ -135,7 +135,8 @@ typedef struct {
     int32_t dmax;
     int64_t* pair_offsets[2];           /* int64[num_clouds+1] per dimension            */
     vr_pair* pairs[2];
-    int32_t* critical_edges[2];         /* 4 per pair if VR_CRITICAL_EDGES, else NULL   */
+    int32_t* critical_edges[2];         /* 4 per pair if VR_CRITICAL_EDGES, else NULL;
+                                           rows of the packed `pts` array (not cloud-local) */
     float* thresholds;                  /* float[num_clouds]: threshold used per cloud  */
 } vr_batch_result;
 

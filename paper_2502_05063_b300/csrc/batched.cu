@@ -617,8 +617,8 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
 // out[off[i] .. off[i+1]), converted to float values.
 __global__ void k_batch_gather(const PairRec* __restrict__ recs, const int32_t* __restrict__ edges,
                                const int64_t* __restrict__ start, const int32_t* __restrict__ count,
-                               const int64_t* __restrict__ off, int num, vr_pair* __restrict__ out,
-                               int32_t* __restrict__ out_edges) {
+                               const int64_t* __restrict__ off, const int64_t* __restrict__ poffs, int num,
+                               vr_pair* __restrict__ out, int32_t* __restrict__ out_edges) {
     for (int cl = blockIdx.x; cl < num; cl += gridDim.x) {
         const int64_t s = start[cl], o = off[cl];
         const int cnt = count[cl];
@@ -630,8 +630,11 @@ __global__ void k_batch_gather(const PairRec* __restrict__ recs, const int32_t* 
             v.birth_simplex = r.birth_cidx;
             v.death_simplex = r.death_cidx;
             out[o + i] = v;
-            if (out_edges)
-                for (int q = 0; q < 4; ++q) out_edges[4 * (o + i) + q] = edges[4 * (s + i) + q];
+            if (out_edges)  // rows of the packed point array
+                for (int q = 0; q < 4; ++q) {
+                    const int32_t e = edges[4 * (s + i) + q];
+                    out_edges[4 * (o + i) + q] = e >= 0 ? (int32_t)(e + poffs[cl]) : -1;
+                }
         }
     }
 }
@@ -719,7 +722,8 @@ void record_launches(BatchPlan& P, cudaStream_t s) {
     for (int p = 0; p <= P.dmax; ++p) {
         k_exclusive_scan_i64<<<1, 1024, 0, s>>>(A.count[p], P.num, P.off[p]);
         k_batch_gather<<<std::min(P.num, 4096), 128, 0, s>>>(A.recs[p], A.edges[p], A.start[p], A.count[p], P.off[p],
-                                                             P.num, P.pairs[p], P.want_edges ? P.edges[p] : nullptr);
+                                                             P.offs, P.num, P.pairs[p],
+                                                             P.want_edges ? P.edges[p] : nullptr);
     }
     VR_CUDA(cudaGetLastError());
 }
@@ -1008,8 +1012,11 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
                 for (int i = 0; i < num_clouds; ++i) {
                     if (b < bad.size() && bad[b] == i) {
                         memcpy(res->pairs[p] + off[i], redo[b]->pairs[p], cnt[i] * sizeof(vr_pair));
-                        if (want_edges) memcpy(res->critical_edges[p] + 4 * off[i], redo[b]->critical_edges[p],
-                                               cnt[i] * 4 * sizeof(int32_t));
+                        if (want_edges)
+                            for (int64_t q = 0; q < 4 * cnt[i]; ++q) {
+                                const int32_t e = redo[b]->critical_edges[p][q];
+                                res->critical_edges[p][4 * off[i] + q] = e >= 0 ? (int32_t)(e + offsets[i]) : -1;
+                            }
                         if (p == 0) res->thresholds[i] = redo[b]->threshold;
                         ++b;
                     } else {

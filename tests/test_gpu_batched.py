@@ -53,7 +53,8 @@ def test_batched_equals_single(vr, dmax, thr, flags):
             assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
             if flags & vr.VR_CRITICAL_EDGES:
                 e = bb.critical_edges[p][bb.offsets[p][i]:bb.offsets[p][i + 1]]
-                assert e.tolist() == single.critical_edges[p].tolist(), (i, p)
+                local = np.where(e >= 0, e - offs[i], -1)  # batched edges index the packed array
+                assert local.tolist() == single.critical_edges[p].tolist(), (i, p)
         assert bb.thresholds[i] == np.float32(single.threshold)
 
 
