@@ -126,6 +126,67 @@ def cpu_oracle_throughput(n: int):
     return candidates(n, 2) / dt, dt
 
 
+def batched_metrics(stream, steps=3):
+    """The batched forms: 4096 clouds (forward, H0-H1) and 256 clouds of 128
+    points in R^2 (forward + backward of sum (death - birth)^2 over H1), each in
+    clouds/s, against a loop of per-cloud calls of the same library."""
+    import torch
+    from paper_2502_05063_b300 import autograd, synth, vr
+
+    def timeit(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    clouds, _ = synth.batch_clouds()
+    pts, offs = synth.pack(clouds)
+    dev = torch.from_numpy(pts).cuda()
+    fwd_ms = timeit(lambda: vr.barcodes_batched(dev, offs, dmax=1, stream=stream), steps)
+    sample = [torch.from_numpy(c).cuda() for c in clouds[::32]]
+    loop_ms = timeit(lambda: [vr.barcodes(points=d, dmax=1, stream=stream) for d in sample], 1) / len(sample)
+
+    circ = synth.circles()
+    cp, co = synth.pack(circ)
+    x = torch.from_numpy(cp).cuda()
+
+    def fwd_bwd_batched():
+        xx = x.detach().requires_grad_(True)
+        out = autograd.VRDiagramBatched.apply(xx, co, 1)
+        h1 = out[1]
+        fin = torch.isfinite(h1[:, 1])
+        ((h1[fin, 1] - h1[fin, 0]) ** 2).sum().backward()
+
+    singles = [torch.from_numpy(c).cuda() for c in circ[::8]]
+
+    def fwd_bwd_loop():
+        for d in singles:
+            xx = d.detach().requires_grad_(True)
+            h1 = autograd.VRDiagram.apply(xx, 1)[1]
+            fin = torch.isfinite(h1[:, 1])
+            ((h1[fin, 1] - h1[fin, 0]) ** 2).sum().backward()
+
+    fb_ms = timeit(fwd_bwd_batched, steps)
+    fb_loop_ms = timeit(fwd_bwd_loop, 1) / len(singles)
+    return {
+        "batch4096_forward": {"clouds_per_s": len(clouds) / (fwd_ms / 1000), "ms_per_batch": fwd_ms,
+                              "per_cloud_loop_clouds_per_s": 1000 / loop_ms, "speedup_vs_loop": loop_ms * len(clouds) / fwd_ms,
+                              "workload": "4096 clouds, n~U{32..256}, circle/sphere/cube in R^3, H0-H1, seed 3",
+                              "loop_sample": "every 32nd cloud, one vr_barcodes call each"},
+        "circles256_fwd_bwd": {"clouds_per_s": len(circ) / (fb_ms / 1000), "ms_per_batch": fb_ms,
+                               "per_cloud_loop_clouds_per_s": 1000 / fb_loop_ms,
+                               "speedup_vs_loop": fb_loop_ms * len(circ) / fb_ms,
+                               "workload": "256 noisy circles, n=128 in R^2, sigma 0.1, seed 4; loss sum over H1 of "
+                                           "(death-birth)^2; forward+backward",
+                               "loop_sample": "every 8th cloud, VRDiagram forward+backward each"},
+    }
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -272,6 +333,8 @@ def run_ours(args):
                                                                  "additions", "cofacets_scanned")}
                    for p in range(1, dmax + 1)},
     }
+    if not args.no_batched:
+        line["batched"] = batched_metrics(stream)
     if world == 1 and not args.no_cpu_baseline:
         v, dt = cpu_oracle_throughput(CPU_SAMPLE_N)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
@@ -304,6 +367,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurements")
     ap.add_argument("--single", action="store_true",
                     help="one untimed call of the workload (for profiler captures), prints its stage counts")
     args = ap.parse_args()
