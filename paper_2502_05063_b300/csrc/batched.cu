@@ -547,7 +547,9 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             __syncthreads();
             bool ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, s);
             uint64_t key = EMPTY;
+            unsigned long long col_adds = 0;
             while (ok) {
+                if (++col_adds > (1ull << 22)) { ok = false; break; }  // far beyond any column: flag the cloud
                 if (S.fsize == 0 && !heavy_refill(S, back, 32 + TRI_BITS)) { key = EMPTY; break; }
                 key = S.buf[S.cur][0];
                 if (!heavy_owner<1>(c, S, key, self_key)) break;

@@ -189,7 +189,12 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
         if (done >= budget) { st = ST_BUDGET; break; }
         if (S.flag == 1) {
             const int64_t opos = S.opos;
-            if (c.rc_len[opos]) {
+            const uint32_t os = slot_of[opos];
+            if (os != 0xFFFFFFFFu && hs.init[os] && hs.adds[os] > 0) {
+                // owner finished by this engine: add its reduced form, front then back
+                ok = heavy_add_multiset(S, B, hs.bcap, hs.F + (int64_t)os * FC, hs.fsize[os]) &&
+                     heavy_add_multiset(S, B, hs.bcap, hs.B + (int64_t)os * hs.bcap, hs.bsize[os]);
+            } else if (c.rc_len[opos]) {
                 ok = heavy_add_stored(c, S, B, hs.bcap, opos);
             } else {
                 Simplex<P> o;
@@ -317,6 +322,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         h.adds = ws.alloc_n<uint32_t>(nslot);
         h.prof = log_enabled() ? ws.zeros_n<unsigned long long>(8) : nullptr;
         uint32_t* slot_of = ws.alloc_n<uint32_t>(m);
+        VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));  // no slot: phase-1 columns
         k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
         int budget = 64;
         while (u > 0) {
@@ -334,6 +340,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
             uint32_t* t = U; U = Un; Un = t;
             const bool stalled = un == u;
             u = un;
+            if (stalled && budget >= (1 << 22)) throw Error{VR_ERR_INTERNAL};  // no column can need this many
             if (stalled && first == ST_OVERFLOW) {
                 // the first column outgrew its back buffer: give the remaining
                 // columns the whole arena (they restart from scratch)
@@ -341,6 +348,8 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 if (nb <= h.bcap) throw Error{VR_ERR_OOM};
                 h.bcap = std::min<int64_t>(nb, (int64_t)1 << 27);
                 h.B = ws.alloc_n<uint64_t>((size_t)u * h.bcap);
+                // slots are reassigned: finished columns lose their stored forms
+                VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));
                 k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
                 VR_CUDA(cudaGetLastError());
             }

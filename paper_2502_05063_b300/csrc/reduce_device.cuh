@@ -615,48 +615,54 @@ __device__ bool heavy_add_run(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
 }
 
 // Refill an empty front from B.  Returns false if the column is zero.
+// The split T comes from a sorted sample of B (its quantile for about
+// 0.7 FKEEP rows), checked by counting; rows below T move to the front,
+// sorted, with rows of even multiplicity cancelled.
 __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
+    (void)keybits;
+    constexpr int NS = 2048;  // samples (fits the spare front buffer)
+    __shared__ int cnt_sh;
+    __shared__ unsigned long long min_sh;
     for (;;) {
         __syncthreads();
         const int64_t bsz = S.bsize;
         if (bsz == 0) return false;
-        // 1. split T with at most REFILL rows below it (MSD radix select)
+        uint64_t* G = S.buf[S.cur ^ 1];
         uint64_t T = EMPTY;
-        if (bsz > REFILL) {
-            uint64_t prefix = 0;
-            int shift = ((keybits + 7) / 8) * 8 - 8;
-            if (shift < 0) shift = 0;
-            int64_t below = 0;
+        if (bsz > (FKEEP * 7) / 10) {
+            // 1. sorted sample
+            const int64_t stride = bsz / NS;
+            for (int i = threadIdx.x; i < NS; i += HT) G[i] = B[(int64_t)i * stride];
+            __syncthreads();
+            block_bitonic(G, NS);
+            int q = (int)((double)FKEEP * 0.7 * NS / (double)bsz);
+            if (q < 1) q = 1;
+            if (q > NS - 1) q = NS - 1;
+            T = G[q];
+            // 2. count rows below T; halve the quantile while too many
             for (;;) {
-                for (int i = threadIdx.x; i < 256; i += HT) S.hist[i] = 0;
+                if (threadIdx.x == 0) { cnt_sh = 0; min_sh = EMPTY; }
                 __syncthreads();
+                int c = 0;
+                uint64_t mn = EMPTY;
                 for (int64_t i = threadIdx.x; i < bsz; i += HT) {
                     const uint64_t k = B[i];
-                    const bool in = shift + 8 >= 64 || (k >> (shift + 8)) == (prefix >> (shift + 8));
-                    if (in) atomicAdd(&S.hist[(k >> shift) & 0xFF], 1u);
+                    c += k < T;
+                    mn = k < mn ? k : mn;
                 }
+                atomicAdd(&cnt_sh, c);
+                atomicMin(reinterpret_cast<unsigned long long*>(&min_sh), (unsigned long long)mn);
                 __syncthreads();
-                if (threadIdx.x == 0) {
-                    int d = 0;
-                    int64_t bl = below;
-                    while (d < 256 && bl + S.hist[d] <= REFILL) bl += S.hist[d++];
-                    const uint64_t hi_mask = (shift + 8 >= 64) ? 0ull : ~((1ull << (shift + 8)) - 1);
-                    S.sel = (prefix & hi_mask) | ((uint64_t)d << shift);
-                    S.flag = bl > 0 ? 1 : (shift == 0 ? 2 : 0);  // 1 done, 2 one key, 0 descend
-                    S.ws[HW] = (int)bl;
-                }
+                const int cnt = cnt_sh;
+                const uint64_t bmin = min_sh;
                 __syncthreads();
-                const int fl = S.flag;
-                if (fl == 1) { T = S.sel; break; }
-                if (fl == 2) { T = S.sel + 1; break; }
-                prefix = S.sel;
-                below = S.ws[HW];
-                shift -= 8;
-                __syncthreads();
+                if (cnt >= 1 && cnt <= FC) break;
+                if (cnt == 0 || q <= 1) { T = bmin + 1; break; }  // the smallest key alone
+                q >>= 1;
+                T = G[q];
             }
         }
-        // 2. move rows < T to the spare buffer (tile by tile: B is compacted in place)
-        uint64_t* G = S.buf[S.cur ^ 1];
+        // 3. move rows < T to the spare buffer (tile by tile: B is compacted in place)
         int nlt = 0;
         int64_t nge = 0;
         for (int64_t base = 0; base < bsz; base += HT) {
@@ -672,7 +678,7 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
             nge += tot >> 16;
         }
         __syncthreads();
-        if (nlt > FC) {  // a single key with more copies than fit: keep its parity only
+        if (nlt > FC) {  // one key with more copies than fit (T = that key + 1): keep its parity only
             if (threadIdx.x == 0) {
                 S.buf[S.cur][0] = T - 1;
                 S.fsize = (nlt & 1) ? 1 : 0;
@@ -688,7 +694,7 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
         for (int i = nlt + threadIdx.x; i < len; i += HT) G[i] = EMPTY;
         __syncthreads();
         block_bitonic(G, len);
-        // 3. keep the rows of odd multiplicity
+        // 4. keep the rows of odd multiplicity
         uint64_t* F = S.buf[S.cur];
         const int chunk = (nlt + HT - 1) / HT;
         const int c0 = min(nlt, (int)threadIdx.x * chunk), c1 = min(nlt, c0 + chunk);
@@ -764,6 +770,44 @@ __device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_
         for (int i = threadIdx.x; i < cnt; i += HT) S.stage[i] = run[base + i];
         __syncthreads();
         if (!heavy_add_run(S, B, bcap, cnt)) return false;
+    }
+    return true;
+}
+
+// W <- W + R_o where R_o = rows[0..len) is any multiset of rows (for example
+// the front and the unsorted back of a column finished by the block engine):
+// each chunk is sorted and its rows of even multiplicity cancel before the
+// chunk is added; rows repeated across chunks cancel in the front or later.
+__device__ bool heavy_add_multiset(HeavySmem& S, uint64_t* B, int64_t bcap, const uint64_t* rows, int64_t len) {
+    for (int64_t base = 0; base < len; base += HSTAGE) {
+        const int cnt = (int)min((int64_t)HSTAGE, len - base);
+        for (int i = threadIdx.x; i < cnt; i += HT) S.stage[i] = rows[base + i];
+        __syncthreads();
+        stage_sort(S, cnt);
+        // keep one row per run of odd length (chunk is at most HSTAGE = 2 * HT rows)
+        bool keep0 = false, keep1 = false;
+        const int i0 = threadIdx.x, i1 = threadIdx.x + HT;
+        uint64_t v0 = 0, v1 = 0;
+        if (i0 < cnt && (i0 == 0 || S.stage[i0 - 1] != S.stage[i0])) {
+            int e = i0;
+            while (e + 1 < cnt && S.stage[e + 1] == S.stage[i0]) ++e;
+            keep0 = ((e - i0 + 1) & 1) != 0;
+            v0 = S.stage[i0];
+        }
+        if (i1 < cnt && (S.stage[i1 - 1] != S.stage[i1])) {
+            int e = i1;
+            while (e + 1 < cnt && S.stage[e + 1] == S.stage[i1]) ++e;
+            keep1 = ((e - i1 + 1) & 1) != 0;
+            v1 = S.stage[i1];
+        }
+        // rows 0..HT-1 first, then HT..2HT-1, so the kept rows stay in order
+        int tot0, tot1;
+        const int pos0 = block_excl_scan((int)keep0, S.ws, &tot0);  // syncs: all reads are done
+        const int pos1 = block_excl_scan((int)keep1, S.ws, &tot1);
+        if (keep0) S.stage[pos0] = v0;
+        if (keep1) S.stage[tot0 + pos1] = v1;
+        __syncthreads();
+        if (!heavy_add_run(S, B, bcap, tot0 + tot1)) return false;
     }
     return true;
 }
