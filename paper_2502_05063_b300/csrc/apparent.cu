@@ -53,100 +53,158 @@ k_filtration_apparent(RankMatrix R, Binom B, uint32_t thr, const uint32_t* __res
     const int64_t n = R.n;
     unsigned long long c_above = 0, c_cleared = 0, c_kept = 0, c_app = 0, c_scan = 0, c_facet = 0;
 
+    constexpr int NPS = NV * (NV - 1) / 2;    // vertex pairs of s
+    constexpr int K_LANE = 32;                 // vertices each lane tests for its own column first
     for (uint64_t chunk = warp; chunk * 32 < num_cand; chunk += nwarps) {
         const uint64_t c = chunk * 32 + lane;
         int v[NV];
+        uint32_t pr[NPS > 0 ? NPS : 1];  // ranks of the pairs of s, pair k = (a, b), a > b, in pair_of order
         uint32_t r = 0;
         bool kept = false;
         if (c < num_cand) {
             decode_simplex<P>(B, c, n - 1, v);
+            int k = 0;
 #pragma unroll
             for (int a = 1; a < NV; ++a)
 #pragma unroll
-                for (int b = 0; b < a; ++b) r = max(r, R(v[a], v[b]));
+                for (int b = 0; b < a; ++b) {
+                    pr[k] = R(v[a], v[b]);
+                    r = max(r, pr[k]);
+                    ++k;
+                }
             if (r > thr) ++c_above;
             else if (clear_bits && ((__ldg(clear_bits + (c >> 5)) >> (c & 31)) & 1u)) ++c_cleared;
             else { kept = true; ++c_kept; }
         }
-        uint32_t kmask = __ballot_sync(0xffffffffu, kept);
-        while (kmask) {
-            const int src = __ffs(kmask) - 1;
-            kmask &= kmask - 1;
+        // 1. lane-parallel: each lane tests w = n-1, n-2, ... for its own column
+        bool active = kept;
+        int64_t wf = -1;
+        uint32_t rw[NV];  // ranks R(v[a], wf) at the hit
+#pragma unroll
+        for (int a = 0; a < NV; ++a) rw[a] = 0;
+        int steps = 0;
+        for (int step = 0; step < K_LANE; ++step) {
+            const int64_t w = n - 1 - step;
+            if (w < 0 || !__any_sync(0xffffffffu, active)) break;
+            ++steps;
+            if (active) {
+                bool ok = true;
+#pragma unroll
+                for (int a = 0; a < NV; ++a) ok = ok && (w != v[a]);
+                if (ok) {
+                    uint32_t rr[NV];
+#pragma unroll
+                    for (int a = 0; a < NV; ++a) rr[a] = R(v[a], w);
+#pragma unroll
+                    for (int a = 0; a < NV; ++a) ok = ok && (rr[a] <= r);
+                    if (ok) {
+                        wf = w;
+                        active = false;
+#pragma unroll
+                        for (int a = 0; a < NV; ++a) rw[a] = rr[a];
+                    }
+                }
+            }
+        }
+        if (kept) c_scan += wf >= 0 ? (unsigned long long)(n - wf) : (unsigned long long)steps;
+        // 2. columns still open: warp-cooperative search over the remaining vertices
+        const int64_t base0 = n - 1 - K_LANE;
+        uint32_t rem = __ballot_sync(0xffffffffu, active && base0 >= 0);
+        while (rem) {
+            const int src = __ffs(rem) - 1;
+            rem &= rem - 1;
             int sv[NV];
 #pragma unroll
             for (int a = 0; a < NV; ++a) sv[a] = __shfl_sync(0xffffffffu, v[a], src);
             const uint32_t sr = __shfl_sync(0xffffffffu, r, src);
-            const uint64_t sc = __shfl_sync(0xffffffffu, c, src);
-            // first cofacet in decreasing index with the same diameter
-            int64_t wf = -1;
-            for (int64_t base = n - 1; base >= 0; base -= 32) {
+            int64_t hit = -1;
+            unsigned long long examined = 0;
+            for (int64_t base = base0; base >= 0; base -= 32) {
                 const int64_t w = base - lane;
                 bool ok = w >= 0;
 #pragma unroll
                 for (int a = 0; a < NV; ++a) ok = ok && (w != sv[a]);
 #pragma unroll
                 for (int a = 0; a < NV; ++a) ok = ok && (R(sv[a], w) <= sr);
-                const uint32_t b = __ballot_sync(0xffffffffu, ok);
-                if (b) {
-                    wf = base - (__ffs(b) - 1);
-                    c_scan += base - wf + 1;  // vertices w examined up to the hit
+                const uint32_t bl = __ballot_sync(0xffffffffu, ok);
+                if (bl) {
+                    hit = base - (__ffs(bl) - 1);
+                    examined += base - hit + 1;
                     break;
                 }
-                c_scan += base >= 31 ? 32 : base + 1;
+                examined += base >= 31 ? 32 : base + 1;
             }
-            if (wf >= 0) ++c_facet;
-            bool apparent = false;
-            if (wf >= 0) {
-                // t = s + wf; lane k tests pair k of t for rank == diam
-                int tv[NV + 1];
+            if (lane == src) {
+                c_scan += examined;
+                if (hit >= 0) {
+                    wf = hit;
 #pragma unroll
-                for (int a = 0; a < NV; ++a) tv[a] = sv[a];
-                tv[NV] = (int)wf;
-                bool eq = false;
-                int pi = 0, pj = 0;
-                if (lane < NPAIR_T) {
-                    pair_of(lane, pi, pj);
-                    eq = R(tv[pi], tv[pj]) == sr;
-                }
-                apparent = true;
-#pragma unroll
-                for (int a = 0; a < NV; ++a) {
-                    if (sv[a] > wf) {  // facet t \ {sv[a]} has a smaller index than s
-                        const bool avoid = eq && pi != a && pj != a;
-                        if (__ballot_sync(0xffffffffu, avoid)) apparent = false;
-                    }
+                    for (int a = 0; a < NV; ++a) rw[a] = R(v[a], wf);
                 }
             }
-            if (lane == 0) {
-                if (apparent) {
-                    ++c_app;
-                    if (o.clear_next || o.zero_pairs) {
-                        // index of t: insert wf into the ascending vertices of s
-                        uint64_t ct = 0;
-                        int k = 0;
-                        bool placed = false;
-                        for (int a = 0; a < NV; ++a) {
-                            if (!placed && wf < sv[a]) { ct += B(wf, k + 1); ++k; placed = true; }
-                            ct += B(sv[a], k + 1);
+        }
+        // 3. facet test in registers: a facet t - {v[a]} with v[a] > wf (smaller index
+        //    than s) must not keep the diameter; its pairs are the pairs of s without
+        //    v[a] and the pairs (wf, v[b]), b != a
+        bool apparent = false;
+        if (kept && wf >= 0) {
+            ++c_facet;
+            apparent = true;
+#pragma unroll
+            for (int a = 0; a < NV; ++a) {
+                if (v[a] > wf) {
+                    bool keeps = false;
+                    int k = 0;
+#pragma unroll
+                    for (int i = 1; i < NV; ++i)
+#pragma unroll
+                        for (int j = 0; j < i; ++j) {
+                            if (i != a && j != a && pr[k] == r) keeps = true;
                             ++k;
                         }
-                        if (!placed) ct += B(wf, k + 1);
-                        if (o.clear_next) atomicOr(o.clear_next + (ct >> 5), 1u << (ct & 31));
-                        if (o.zero_pairs) {
-                            unsigned long long at = atomicAdd(o.num_zero_pairs, 1ull);
-                            PairRec pr;
-                            pr.birth_rank = sr; pr.death_rank = sr;
-                            pr.birth_cidx = sc; pr.death_cidx = (int64_t)ct;
-                            o.zero_pairs[at] = pr;
-                        }
-                    }
-                } else {
-                    unsigned long long at = atomicAdd(o.num_nonapparent, 1ull);
-                    if ((int64_t)at < o.capacity)
-                        o.nonapparent_keys[at] = ((~(uint64_t)sr & rmask) << cidx_bits) | sc;
-                    else
-                        atomicExch(o.dev_err, DEV_CAPACITY);
+#pragma unroll
+                    for (int bb = 0; bb < NV; ++bb)
+                        if (bb != a && rw[bb] == r) keeps = true;
+                    if (keeps) apparent = false;
                 }
+            }
+        }
+        // 4. outputs
+        if (apparent) {
+            ++c_app;
+            if (o.clear_next || o.zero_pairs) {
+                uint64_t ct = 0;  // index of t: wf inserted into the ascending vertices of s
+                int k = 0;
+                bool placed = false;
+#pragma unroll
+                for (int a = 0; a < NV; ++a) {
+                    if (!placed && wf < v[a]) { ct += B(wf, k + 1); ++k; placed = true; }
+                    ct += B(v[a], k + 1);
+                    ++k;
+                }
+                if (!placed) ct += B(wf, k + 1);
+                if (o.clear_next) atomicOr(o.clear_next + (ct >> 5), 1u << (ct & 31));
+                if (o.zero_pairs) {
+                    const unsigned long long at = atomicAdd(o.num_zero_pairs, 1ull);
+                    PairRec prc;
+                    prc.birth_rank = r; prc.death_rank = r;
+                    prc.birth_cidx = c; prc.death_cidx = (int64_t)ct;
+                    o.zero_pairs[at] = prc;
+                }
+            }
+        }
+        const bool nonapp = kept && !apparent;
+        const uint32_t nb = __ballot_sync(0xffffffffu, nonapp);
+        if (nb) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(o.num_nonapparent, (unsigned long long)__popc(nb));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (nonapp) {
+                const unsigned long long at = base + __popc(nb & ((1u << lane) - 1u));
+                if ((int64_t)at < o.capacity)
+                    o.nonapparent_keys[at] = ((~(uint64_t)r & rmask) << cidx_bits) | c;
+                else
+                    atomicExch(o.dev_err, DEV_CAPACITY);
             }
         }
     }
@@ -156,13 +214,16 @@ k_filtration_apparent(RankMatrix R, Binom B, uint32_t thr, const uint32_t* __res
         c_above += __shfl_xor_sync(0xffffffffu, c_above, off);
         c_cleared += __shfl_xor_sync(0xffffffffu, c_cleared, off);
         c_kept += __shfl_xor_sync(0xffffffffu, c_kept, off);
+        c_app += __shfl_xor_sync(0xffffffffu, c_app, off);
+        c_scan += __shfl_xor_sync(0xffffffffu, c_scan, off);
+        c_facet += __shfl_xor_sync(0xffffffffu, c_facet, off);
     }
     if (lane == 0) {
         if (c_above) atomicAdd(o.counters + 0, c_above);
         if (c_cleared) atomicAdd(o.counters + 1, c_cleared);
         if (c_kept) atomicAdd(o.counters + 2, c_kept);
         if (c_app) atomicAdd(o.counters + 3, c_app);
-        if (c_scan) atomicAdd(o.counters + 6, c_scan);    // counted identically on every lane
+        if (c_scan) atomicAdd(o.counters + 6, c_scan);
         if (c_facet) atomicAdd(o.counters + 7, c_facet);
     }
 }
