@@ -358,6 +358,12 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         if (h.prof) {
             VR_CUDA(cudaMemcpyAsync(&hs.p[16], h.prof, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             VR_CUDA(cudaStreamSynchronize(s));
+            unsigned long long hc[4];
+            VR_CUDA(cudaMemcpyFromSymbol(hc, g_heavy_counts, sizeof hc));
+            fprintf(stderr, "[vr] dim%d block engine: %llu refills, %llu rows to front, %llu rows to back, %llu passes\n", P,
+                    hc[0], hc[1], hc[2], hc[3]);
+            const unsigned long long zero[4] = {0, 0, 0, 0};
+            VR_CUDA(cudaMemcpyToSymbol(g_heavy_counts, zero, sizeof zero));
             const double ad = hs.p[20] ? (double)hs.p[20] : 1.0, lk = hs.p[21] ? (double)hs.p[21] : 1.0;
             fprintf(stderr,
                     "[vr] dim%d block engine: %lld additions, %lld lookups; cycles/add %.0f, cycles/lookup %.0f, "

@@ -463,6 +463,9 @@ struct HeavyState {
     unsigned long long* prof;  // VR_LOG only: cycles {refill, lookup, add, resume}, counts {adds, lookups}
 };
 
+// VR_LOG instrumentation of the block engine: {refills, rows to front, rows to back, merges}
+__device__ unsigned long long g_heavy_counts[4];
+
 struct HeavySmem {
     uint64_t buf[2][FC];   // the front and its merge target, swapped after each merge
     uint64_t stage[HSTAGE];
@@ -627,6 +630,7 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
         __syncthreads();
         const int64_t bsz = S.bsize;
         if (bsz == 0) return false;
+        if (threadIdx.x == 0) atomicAdd(&g_heavy_counts[0], 1ull);
         uint64_t* G = S.buf[S.cur ^ 1];
         uint64_t T = EMPTY;
         if (bsz > (FKEEP * 7) / 10) {
@@ -665,15 +669,26 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
         // 3. move rows < T to the spare buffer (tile by tile: B is compacted in place)
         int nlt = 0;
         int64_t nge = 0;
-        for (int64_t base = 0; base < bsz; base += HT) {
-            const int64_t i = base + threadIdx.x;
-            const uint64_t k = i < bsz ? B[i] : EMPTY;
-            const bool lt = i < bsz && k < T;
-            const bool ge = i < bsz && !lt;
+        constexpr int PER = 8;  // rows per thread per tile: one block scan per HT * PER rows
+        for (int64_t base = 0; base < bsz; base += (int64_t)HT * PER) {
+            const int64_t i0 = base + (int64_t)threadIdx.x * PER;
+            uint64_t k[PER];
+            int cl = 0, cg = 0;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                k[q] = i0 + q < bsz ? B[i0 + q] : EMPTY;
+                if (i0 + q < bsz) { if (k[q] < T) ++cl; else ++cg; }
+            }
             int tot;
-            const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
-            if (lt && nlt + (packed & 0xFFFF) < FC) G[nlt + (packed & 0xFFFF)] = k;
-            if (ge) B[nge + (packed >> 16)] = k;
+            const int packed = block_excl_scan(cl | (cg << 16), S.ws, &tot);  // all of the tile is read
+            int pl = nlt + (packed & 0xFFFF);
+            int64_t pg = nge + (packed >> 16);
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                if (i0 + q >= bsz) continue;
+                if (k[q] < T) { if (pl < FC) G[pl] = k[q]; ++pl; }
+                else B[pg++] = k[q];
+            }
             nlt += tot & 0xFFFF;
             nge += tot >> 16;
         }
@@ -748,6 +763,11 @@ __device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, in
         int tot;
         const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
         const int nlt = tot & 0xFFFF, nge = tot >> 16;
+        if (threadIdx.x == 0) {
+            atomicAdd(&g_heavy_counts[1], (unsigned long long)nlt);
+            atomicAdd(&g_heavy_counts[2], (unsigned long long)nge);
+            atomicAdd(&g_heavy_counts[3], 1ull);
+        }
         const int64_t bs = S.bsize;
         if (bs + nge > bcap) return false;
         if (ge) B[bs + (packed >> 16)] = key;
@@ -822,13 +842,13 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
     const uint32_t rt = (uint32_t)(rk >> c.rcb);
     const uint64_t ct = c.rcmask - (rk & c.rcmask);
     if (wid == 0) {
-        int64_t pos = warp_hash_find(c, ct);
+        // a row has at most one owner: test the apparent pair first (the common
+        // case) and probe the hash of finished columns only if it is not one
+        int64_t pos = -1;
         int flag = 0;  // 1 = stored column owner, 2 = candidate apparent owner, 0 = none
         int drop = -1;
         int tv[NT];
-        if (pos >= 0) {
-            flag = 1;
-        } else {
+        {
             decode_simplex<P + 1>(c.B, ct, n - 1, tv);
             bool eq = false;
             int pi = 0, pj = 0;
@@ -857,31 +877,35 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
         }
     }
     __syncthreads();
-    const int flag = S.flag;
-    if (flag == 0) return false;
-    if (flag == 1) {
-        if (threadIdx.x == 0) {
-            const uint64_t okey = c.cols[S.opos];
-            if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL);
+    if (S.flag == 2) {
+        // apparent iff no vertex w above the dropped one keeps the diameter of s'
+        int ov[P + 1];
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ov[q] = S.ov[q];
+        const int64_t wd = S.ov[P + 1];
+        bool older = false;
+        for (int64_t base = n - 1; base > wd; base -= HT) {
+            const int64_t w = base - (int64_t)threadIdx.x;
+            bool ok = w > wd;
+#pragma unroll
+            for (int q = 0; q <= P; ++q) ok = ok && (w != ov[q]);
+#pragma unroll
+            for (int q = 0; q <= P; ++q) ok = ok && (c.R(ov[q], w) <= rt);
+            older = older || ok;
         }
-        return true;
+        if (!__syncthreads_or(older)) return true;
     }
-    // apparent iff no vertex w above the dropped one keeps the diameter of s'
-    int ov[P + 1];
-#pragma unroll
-    for (int q = 0; q <= P; ++q) ov[q] = S.ov[q];
-    const int64_t wd = S.ov[P + 1];
-    bool older = false;
-    for (int64_t base = n - 1; base > wd; base -= HT) {
-        const int64_t w = base - (int64_t)threadIdx.x;
-        bool ok = w > wd;
-#pragma unroll
-        for (int q = 0; q <= P; ++q) ok = ok && (w != ov[q]);
-#pragma unroll
-        for (int q = 0; q <= P; ++q) ok = ok && (c.R(ov[q], w) <= rt);
-        older = older || ok;
+    // not an apparent pair: the pivot of a finished column?
+    if (wid == 0) {
+        const int64_t pos = warp_hash_find(c, ct);
+        if (lane == 0) {
+            S.flag = pos >= 0 ? 1 : 0;
+            S.opos = pos;
+            if (pos >= 0 && !(c.cols[pos] < self_key)) atomicExch(c.err, DEV_INTERNAL);
+        }
     }
-    return !__syncthreads_or(older);
+    __syncthreads();
+    return S.flag == 1;
 }
 
 
