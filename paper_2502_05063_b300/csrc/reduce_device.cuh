@@ -525,9 +525,29 @@ __device__ void block_bitonic(uint64_t* a, int len) {
         }
 }
 
-// Sort stage[0..cnt) ascending (pads to a power of two with EMPTY).
+// Sort stage[0..cnt) ascending.  Up to HT rows: each thread ranks its row by
+// comparing it with every row (broadcast shared reads, stable for equal
+// rows) and places it, which costs one barrier instead of the log^2 barrier
+// stages of a bitonic network; more rows use the bitonic network.
 __device__ void stage_sort(HeavySmem& S, int cnt) {
     if (cnt <= 1) return;
+    if (cnt <= HT && cnt <= HSTAGE / 2) {
+        const int i = threadIdx.x;
+        uint64_t x = 0;
+        int rank = 0;
+        if (i < cnt) {
+            x = S.stage[i];
+            for (int j = 0; j < cnt; ++j) {
+                const uint64_t y = S.stage[j];
+                rank += (y < x) || (y == x && j < i);
+            }
+            S.stage[HSTAGE / 2 + rank] = x;
+        }
+        __syncthreads();
+        if (i < cnt) S.stage[i] = S.stage[HSTAGE / 2 + i];
+        __syncthreads();
+        return;
+    }
     int len = 2;
     while (len < cnt) len <<= 1;
     for (int i = cnt + threadIdx.x; i < len; i += HT) S.stage[i] = EMPTY;
@@ -841,11 +861,14 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
     const int64_t n = c.R.n;
     const uint32_t rt = (uint32_t)(rk >> c.rcb);
     const uint64_t ct = c.rcmask - (rk & c.rcmask);
+    // a row has at most one owner: warp 1 probes the hash of finished columns
+    // while warp 0 prepares the apparent-pair test
+    if (wid == 1) {
+        const int64_t hp = warp_hash_find(c, ct);
+        if (lane == 0) S.opos = hp;
+    }
     if (wid == 0) {
-        // a row has at most one owner: test the apparent pair first (the common
-        // case) and probe the hash of finished columns only if it is not one
-        int64_t pos = -1;
-        int flag = 0;  // 1 = stored column owner, 2 = candidate apparent owner, 0 = none
+        int flag = 0;  // 2 = candidate apparent owner, 0 = none
         int drop = -1;
         int tv[NT];
         {
@@ -866,7 +889,6 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
         }
         if (lane == 0) {
             S.flag = flag;
-            S.opos = pos;
             if (flag == 2) {
                 int k = 0;
                 for (int q = 0; q < NT; ++q)
@@ -877,6 +899,15 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
         }
     }
     __syncthreads();
+    if (S.opos >= 0) {  // the pivot of a finished column
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S.flag = 1;
+            if (!(c.cols[S.opos] < self_key)) atomicExch(c.err, DEV_INTERNAL);
+        }
+        __syncthreads();
+        return true;
+    }
     if (S.flag == 2) {
         // apparent iff no vertex w above the dropped one keeps the diameter of s'
         int ov[P + 1];
@@ -893,19 +924,9 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
             for (int q = 0; q <= P; ++q) ok = ok && (c.R(ov[q], w) <= rt);
             older = older || ok;
         }
-        if (!__syncthreads_or(older)) return true;
+        return !__syncthreads_or(older);
     }
-    // not an apparent pair: the pivot of a finished column?
-    if (wid == 0) {
-        const int64_t pos = warp_hash_find(c, ct);
-        if (lane == 0) {
-            S.flag = pos >= 0 ? 1 : 0;
-            S.opos = pos;
-            if (pos >= 0 && !(c.cols[pos] < self_key)) atomicExch(c.err, DEV_INTERNAL);
-        }
-    }
-    __syncthreads();
-    return S.flag == 1;
+    return false;
 }
 
 
