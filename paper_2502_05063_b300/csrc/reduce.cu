@@ -23,9 +23,17 @@
 // final pivot of any earlier column, and a vector of D_j + span(D_<j) whose
 // low is no earlier column's pivot has the low of the fully reduced column
 // (the argument behind Lemma 5.2.10).  Columns finalized in one round have
-// strictly decreasing keys, hence distinct pivots.  When a round makes no
-// progress or few columns remain, one warp finishes them in order, which is
-// Algorithm 12 verbatim.
+// strictly decreasing keys, hence distinct pivots.
+//
+// Phase 1: one warp per column, at most 8 additions, all columns at once;
+// finished columns that needed additions keep their reduced form.  Phase 2:
+// one block per remaining column (the front/back engine of
+// reduce_device.cuh), state kept across rounds, budgets doubling; a column
+// whose pivot belongs to a column finished in phase 2 adds that column's
+// reduced form.  The first unfinished column can never be blocked, so every
+// round with enough budget makes progress; a stall with an overflowing first
+// column moves the remaining columns to larger buffers (VR_ERR_OOM if they
+// cannot grow).
 //
 // Pivot lookup (the paper's two-layer store, Fig 5.10): first a device hash
 // of pivots found by this reduction, then the apparent pairs, which are not
@@ -240,28 +248,6 @@ __global__ void k_assign_slots(const uint32_t* __restrict__ U, int64_t u, uint32
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x) {
         slot_of[U[k]] = (uint32_t)k;
         init[k] = 0;
-    }
-}
-
-// One warp finishes the remaining columns in order (Algorithm 12 verbatim).
-template <int P>
-__global__ void __launch_bounds__(32)
-k_reduce_seq(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, uint64_t* bufA, uint64_t* bufB, int64_t cap) {
-    __shared__ uint64_t stage[STAGE];
-    const int lane = threadIdx.x & 31;
-    for (int64_t k = 0; k < u; ++k) {
-        const int64_t j = U[k];
-        uint64_t key;
-        uint8_t st;
-        uint32_t ad;
-        reduce_one<P>(c, j, 0x7FFFFFFF, stage, bufA, bufB, cap, key, st, ad);
-        if (st != ST_COMPLETE) {
-            if (lane == 0) atomicExch(c.err, DEV_CAPACITY);
-            return;
-        }
-        if (lane == 0) finish_column(c, e, j, key, ad);
-        __threadfence_block();
-        __syncwarp();
     }
 }
 
