@@ -150,7 +150,7 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
 
 
 template <int P>
-__global__ void __launch_bounds__(HT)
+__global__ void __launch_bounds__(HT, 1)
 k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t* __restrict__ slot_of,
                HeavyState hs, int budget, int keybits, uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status,
                uint32_t* __restrict__ adds_out) {
@@ -164,6 +164,8 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
     const uint64_t self_key = c.cols[j];
     Simplex<P> s;
     load_col<P>(c, self_key, s);
+    if (threadIdx.x < 10) S.tp[threadIdx.x] = 0;
+    __syncthreads();
     uint32_t adds;
     bool ok = true;
     if (!hs.init[slot]) {
@@ -228,6 +230,15 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
         atomicAdd(hs.prof + 3, (unsigned long long)(clock64() - t_resume - t_ref - t_look - t_add));
         atomicAdd(hs.prof + 4, (unsigned long long)done);
         atomicAdd(hs.prof + 5, (unsigned long long)n_look);
+        atomicMax(hs.prof + 6, (unsigned long long)done);
+        atomicMax(hs.prof + 7, (unsigned long long)(clock64() - t_resume));
+        const long long tot = clock64() - t_resume;
+        if (tot > 4000000)
+            printf("[vr] dim%d col %lld: %d adds %lld cycles: refill %lld lookup %lld add %lld | gen %lld sort %lld "
+                   "merge %lld multiset %lld (%lld) | refill sample %lld count %lld compact %lld sort %lld (%lld) "
+                   "back %lld front %d\n",
+                   P, (long long)j, done, tot, t_ref, t_look, t_add, S.tp[0], S.tp[1], S.tp[2], S.tp[3], S.tp[8],
+                   S.tp[4], S.tp[5], S.tp[6], S.tp[7], S.tp[9], (long long)S.bsize, S.fsize);
     }
     if (!ok) st = ST_OVERFLOW;  // key holds the last consistent pivot, a valid bound
     for (int i = threadIdx.x; i < S.fsize && ok; i += HT) hs.F[slot * FC + i] = S.buf[S.cur][i];
@@ -311,18 +322,33 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));  // no slot: phase-1 columns
         k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
         int budget = 64;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        if (h.prof) { VR_CUDA(cudaEventCreate(&ev[0])); VR_CUDA(cudaEventCreate(&ev[1])); }
         while (u > 0) {
+            if (h.prof) {
+                VR_CUDA(cudaMemsetAsync(h.prof + 6, 0, 2 * sizeof(unsigned long long), s));
+                VR_CUDA(cudaEventRecord(ev[0], s));
+            }
             k_reduce_heavy<P><<<(unsigned)u, HT, smem, s>>>(c, U, u, slot_of, h, budget, keybits, cur_key, status, adds);
+            if (h.prof) VR_CUDA(cudaEventRecord(ev[1], s));
             k_finalize<<<1, 1024, 0, s>>>(c, e, U, u, cur_key, status, adds, Un, ctr + 1, ctr + 2);
             VR_CUDA(cudaGetLastError());
             VR_CUDA(cudaMemcpyAsync(&hs.p[8], ctr + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            if (h.prof)
+                VR_CUDA(cudaMemcpyAsync(&hs.p[24], h.prof + 6, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             VR_CUDA(cudaStreamSynchronize(s));
             const int64_t un = hs.p[8];
             const int64_t first = hs.p[9];
             ++rounds;
-            if (log_enabled())
-                fprintf(stderr, "[vr] dim%d block round %d: budget %d bcap %lld: %lld -> %lld unfinished\n", P,
-                        rounds, budget, (long long)h.bcap, (long long)u, (long long)un);
+            if (log_enabled()) {
+                float ms = 0.f;
+                if (h.prof) VR_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+                fprintf(stderr,
+                        "[vr] dim%d block round %d: budget %d bcap %lld: %lld -> %lld unfinished; %.3f ms, "
+                        "max additions %lld, max block cycles %lld\n",
+                        P, rounds, budget, (long long)h.bcap, (long long)u, (long long)un, ms, (long long)hs.p[24],
+                        (long long)hs.p[25]);
+            }
             uint32_t* t = U; U = Un; Un = t;
             const bool stalled = un == u;
             u = un;
@@ -342,6 +368,8 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
             if (budget < (1 << 24)) budget *= 2;
         }
         if (h.prof) {
+            VR_CUDA(cudaEventDestroy(ev[0]));
+            VR_CUDA(cudaEventDestroy(ev[1]));
             VR_CUDA(cudaMemcpyAsync(&hs.p[16], h.prof, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             VR_CUDA(cudaStreamSynchronize(s));
             unsigned long long hc[4];

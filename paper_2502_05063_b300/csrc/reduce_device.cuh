@@ -55,7 +55,7 @@ template <int P>
 __device__ __forceinline__ void load_col(const Ctx& c, uint64_t key, Simplex<P>& s) {
     s.cidx = key & c.cmask;
     s.r = (uint32_t)((~(key >> c.cb)) & c.rmask);
-    decode_simplex<P>(c.B, s.cidx, c.R.n - 1, s.v);
+    warp_decode_simplex<P>(c.B, s.cidx, c.R.n - 1, s.v);  // callers are whole warps
 }
 
 template <int P>
@@ -268,7 +268,7 @@ __device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex
     }
     // 2. apparent pairs (Def 5.3.4), recomputed
     int tv[NT];
-    decode_simplex<P + 1>(c.B, ct, n - 1, tv);
+    warp_decode_simplex<P + 1>(c.B, ct, n - 1, tv);
     bool eq = false;
     int pi = 0, pj = 0;
     if (lane < NPAIR) {
@@ -438,10 +438,10 @@ __device__ void finish_column(const Ctx& c, const Emit& e, int64_t j, uint64_t k
 // split at a key Ks: the front F (rows < Ks, sorted, unique, at most FC of
 // them) lives in shared memory and is the only part the pivot search reads;
 // the back B (rows >= Ks) is an unsorted multiset in global memory to which
-// new rows are appended without sorting.  When F runs empty, a most-
-// significant-digit radix select over B finds a split T with at most FC/2
-// rows below it; those rows are sorted, rows of even multiplicity cancel
-// (Z/2), and the rest become the new front with Ks = T.  An addition thus
+// new rows are appended without sorting.  When F runs empty, a sampled
+// split T with at most FC rows below it is found; those rows are taken out
+// of B (leaving holes), sorted, rows of even multiplicity cancel (Z/2), and
+// the rest become the new front with Ks = T.  An addition thus
 // costs O(rows added + |F|), independent of the column's size.
 // ---------------------------------------------------------------------------
 constexpr int HT = 512;          // threads per block
@@ -450,6 +450,8 @@ constexpr int FC = 4096;         // front capacity
 constexpr int FKEEP = FC - 1024; // front size kept after a spill
 constexpr int HSTAGE = 1024;     // rows generated or copied per pass (power of two >= HT)
 constexpr int REFILL = FC / 2;   // rows promoted from the back per refill (at most)
+static_assert(HSTAGE == 2 * HT, "a merge takes two run rows per thread");
+static_assert(FC < (1 << 16) && HSTAGE < (1 << 15), "merge positions are packed in 16 + 15 bits");
 
 struct HeavyState {
     uint64_t* F;       // slots x FC, the front saved between rounds
@@ -469,6 +471,7 @@ __device__ unsigned long long g_heavy_counts[4];
 struct HeavySmem {
     uint64_t buf[2][FC];   // the front and its merge target, swapped after each merge
     uint64_t stage[HSTAGE];
+    uint32_t mq[HSTAGE];   // merge: per run row, its place in the front | cancellations before it | cancels
     int ws[HW + 1];
     uint32_t hist[256];
     uint64_t Ks;
@@ -480,7 +483,10 @@ struct HeavySmem {
     int ov[VR_MAX_DIM + 2];
     uint32_t orank;
     uint64_t sel;          // radix-select result
+    long long tp[10];      // VR_LOG only (thread 0): sub-phase cycles
 };
+#define HPROF_T0() long long _hp_t = clock64()
+#define HPROF_LAP(i) do { if (threadIdx.x == 0) { long long _n = clock64(); S.tp[i] += _n - _hp_t; _hp_t = _n; } } while (0)
 
 // exclusive block scan of one int per thread; *total receives the sum
 __device__ __forceinline__ int block_excl_scan(int x, int* ws, int* total) {
@@ -576,48 +582,63 @@ __device__ bool heavy_append(HeavySmem& S, uint64_t* B, int64_t bcap, const uint
 }
 
 // front <- front XOR stage[0..b), stage sorted, unique and entirely below Ks.
+// Merge by position: run row k, with lower bound q_k in the front and E_k
+// earlier run rows that cancel a front row, lands at q_k + k - 2 E_k (or
+// cancels F[q_k]); front row i lands at i + r_i - 2 E(i), r_i run rows below
+// it and E(i) cancellations before it, which each thread reads off the
+// sorted q's for its chunk of the front.
 __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
     if (b == 0) return true;
     const uint64_t* run = S.stage;
     const uint64_t* F = S.buf[S.cur];
     uint64_t* F2 = S.buf[S.cur ^ 1];
     const int a = S.fsize;
-    // rows of F below run[0] keep their place
-    const int p0 = lower_bound_sm(F, a, run[0]);
-    for (int i = threadIdx.x; i < p0; i += HT) F2[i] = F[i];
-    const int rest = a - p0;
-    const int chunkF = (rest + HT - 1) / HT;
-    const int f0 = p0 + min(rest, (int)threadIdx.x * chunkF), f1 = min(a, f0 + chunkF);
-    int mloc = 0;
-    for (int i = f0; i < f1; ++i) {
-        int q = lower_bound_sm(run, b, F[i]);
-        mloc += (q < b && run[q] == F[i]);
+    // 1. run rows 2t and 2t+1 (b <= HSTAGE = 2 HT)
+    const int k0 = 2 * (int)threadIdx.x;
+    int q0 = 0, q1 = 0;
+    bool e0 = false, e1 = false;
+    if (k0 < b) {
+        q0 = lower_bound_sm(F, a, run[k0]);
+        e0 = q0 < a && F[q0] == run[k0];
     }
-    int mtot;
-    int m = block_excl_scan(mloc, S.ws, &mtot);
-    for (int i = f0; i < f1; ++i) {
-        const uint64_t x = F[i];
-        const int q = lower_bound_sm(run, b, x);
-        if (q < b && run[q] == x) { ++m; continue; }
-        F2[i + q - 2 * m] = x;
+    if (k0 + 1 < b) {
+        q1 = lower_bound_sm(F, a, run[k0 + 1]);
+        e1 = q1 < a && F[q1] == run[k0 + 1];
     }
-    const int chunkR = (b + HT - 1) / HT;
-    const int r0 = min(b, (int)threadIdx.x * chunkR), r1 = min(b, r0 + chunkR);
-    int mloc2 = 0;
-    for (int k = r0; k < r1; ++k) {
-        const int q = lower_bound_sm(F, a, run[k]);
-        mloc2 += (q < a && F[q] == run[k]);
+    int etot;
+    const int ex = block_excl_scan((int)e0 + (int)e1, S.ws, &etot);
+    if (k0 < b) {
+        S.mq[k0] = (uint32_t)q0 | ((uint32_t)ex << 16) | (e0 ? 0x80000000u : 0u);
+        if (!e0) F2[q0 + k0 - 2 * ex] = run[k0];
     }
-    int mt2;
-    int m2 = block_excl_scan(mloc2, S.ws, &mt2);
-    for (int k = r0; k < r1; ++k) {
-        const uint64_t y = run[k];
-        const int q = lower_bound_sm(F, a, y);
-        if (q < a && F[q] == y) { ++m2; continue; }
-        F2[k + q - 2 * m2] = y;
+    if (k0 + 1 < b) {
+        const int ex1 = ex + (int)e0;
+        S.mq[k0 + 1] = (uint32_t)q1 | ((uint32_t)ex1 << 16) | (e1 ? 0x80000000u : 0u);
+        if (!e1) F2[q1 + k0 + 1 - 2 * ex1] = run[k0 + 1];
     }
     __syncthreads();
-    int na = a + b - 2 * mtot;
+    // 2. the front, a contiguous chunk per thread
+    const int chunk = (a + HT - 1) / HT;
+    const int f0 = min(a, (int)threadIdx.x * chunk), f1 = min(a, f0 + chunk);
+    if (f0 < f1) {
+        int lo = 0, hi = b;  // first run row with q >= f0
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((int)(S.mq[mid] & 0xFFFFu) < f0) lo = mid + 1; else hi = mid;
+        }
+        int k = lo;
+        int E = k < b ? (int)((S.mq[k] >> 16) & 0x7FFFu) : etot;
+        for (int i = f0; i < f1; ++i) {
+            uint32_t m;
+            while (k < b && (int)((m = S.mq[k]) & 0xFFFFu) < i) { E += (int)(m >> 31); ++k; }
+            int k2 = k;
+            bool canc = false;
+            while (k2 < b && (int)((m = S.mq[k2]) & 0xFFFFu) == i) { canc = canc || (m >> 31); ++k2; }
+            if (!canc) F2[i + k2 - 2 * E] = F[i];
+        }
+    }
+    __syncthreads();
+    int na = a + b - 2 * etot;
     if (threadIdx.x == 0) S.cur ^= 1;
     __syncthreads();
     if (na > FKEEP) {  // spill the top of the front to B and lower the split
@@ -637,125 +658,204 @@ __device__ bool heavy_add_run(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
     return heavy_merge_front(S, B, bcap, lo);
 }
 
+// Remove the holes (EMPTY) from B in place, keeping the order of the rest.
+__device__ void heavy_compact_back(HeavySmem& S, uint64_t* B) {
+    const int64_t bsz = S.bsize;
+    constexpr int PER = 8;
+    // the next tile is loaded before this one is written back: writes land
+    // below the current tile's end, so they never touch the rows read
+    uint64_t nk[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int64_t i = (int64_t)q * HT + threadIdx.x;
+        nk[q] = i < bsz ? B[i] : EMPTY;
+    }
+    int64_t nkeep = 0;
+    for (int64_t base = 0; base < bsz; base += (int64_t)HT * PER) {
+        uint64_t k[PER];
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            k[q] = nk[q];
+            cnt += k[q] != EMPTY;
+        }
+        if (base + (int64_t)HT * PER < bsz) {
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int64_t i = base + (int64_t)HT * (PER + q) + threadIdx.x;
+                nk[q] = i < bsz ? B[i] : EMPTY;
+            }
+        }
+        int tot;
+        int64_t pos = nkeep + block_excl_scan(cnt, S.ws, &tot);  // all of the tile is read
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (k[q] != EMPTY) B[pos++] = k[q];
+        nkeep += tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) S.bsize = nkeep;
+    __syncthreads();
+}
+
 // Refill an empty front from B.  Returns false if the column is zero.
 // The split T comes from a sorted sample of B (its quantile for about
-// 0.7 FKEEP rows), checked by counting; rows below T move to the front,
-// sorted, with rows of even multiplicity cancelled.
+// 0.7 FKEEP rows); one pass over B collects the positions of the rows below
+// T (at most FC of them, else T is lowered and the pass repeated), then
+// those rows are gathered, replaced by holes (EMPTY, above every row key),
+// sorted, and the rows of odd multiplicity become the front (Z/2).  B is
+// only read in full; it is compacted once holes make up half of it.
 __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
     (void)keybits;
-    constexpr int NS = 2048;  // samples (fits the spare front buffer)
+    constexpr int NS = 2048;  // samples (fit the empty front buffer)
+    constexpr int UN = 8;     // independent loads in flight per thread
+    static_assert(NS <= FC, "the sample lives in the front buffer");
     __shared__ int cnt_sh;
     __shared__ unsigned long long min_sh;
+    __shared__ unsigned long long holes_sh;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     for (;;) {
         __syncthreads();
         const int64_t bsz = S.bsize;
         if (bsz == 0) return false;
-        if (threadIdx.x == 0) atomicAdd(&g_heavy_counts[0], 1ull);
-        uint64_t* G = S.buf[S.cur ^ 1];
+        HPROF_T0();
+        if (threadIdx.x == 0) { atomicAdd(&g_heavy_counts[0], 1ull); S.tp[9] += 1; }
+        uint64_t* Sm = S.buf[S.cur];       // the sample (the front is empty)
+        uint64_t* G = S.buf[S.cur ^ 1];    // positions, then rows, below T
         uint64_t T = EMPTY;
+        int q = 0;
         if (bsz > (FKEEP * 7) / 10) {
-            // 1. sorted sample
             const int64_t stride = bsz / NS;
-            for (int i = threadIdx.x; i < NS; i += HT) G[i] = B[(int64_t)i * stride];
+            for (int i = threadIdx.x; i < NS; i += HT) Sm[i] = B[(int64_t)i * stride];
             __syncthreads();
-            block_bitonic(G, NS);
-            int q = (int)((double)FKEEP * 0.7 * NS / (double)bsz);
+            block_bitonic(Sm, NS);
+            q = (int)((double)FKEEP * 0.7 * NS / (double)bsz);
             if (q < 1) q = 1;
             if (q > NS - 1) q = NS - 1;
-            T = G[q];
-            // 2. count rows below T; halve the quantile while too many
-            for (;;) {
-                if (threadIdx.x == 0) { cnt_sh = 0; min_sh = EMPTY; }
-                __syncthreads();
-                int c = 0;
-                uint64_t mn = EMPTY;
-                for (int64_t i = threadIdx.x; i < bsz; i += HT) {
-                    const uint64_t k = B[i];
-                    c += k < T;
-                    mn = k < mn ? k : mn;
+            T = Sm[q];
+        }
+        HPROF_LAP(4);
+        int cnt;
+        uint64_t bmin;
+        int64_t holes;
+        for (;;) {
+            if (threadIdx.x == 0) { cnt_sh = 0; min_sh = EMPTY; holes_sh = 0; }
+            __syncthreads();
+            uint64_t mn = EMPTY;
+            int hl = 0;
+            // warp-uniform trip count: every lane reaches the ballots
+            for (int64_t w0 = (int64_t)threadIdx.x - lane; w0 < bsz; w0 += (int64_t)HT * UN) {
+                uint64_t kk[UN];
+#pragma unroll
+                for (int u = 0; u < UN; ++u) {
+                    const int64_t i = w0 + (int64_t)u * HT + lane;
+                    kk[u] = i < bsz ? B[i] : EMPTY;
+                    hl += i < bsz && kk[u] == EMPTY;
                 }
-                atomicAdd(&cnt_sh, c);
-                atomicMin(reinterpret_cast<unsigned long long*>(&min_sh), (unsigned long long)mn);
+#pragma unroll
+                for (int u = 0; u < UN; ++u) {
+                    const bool lt = kk[u] < T;
+                    mn = kk[u] < mn ? kk[u] : mn;
+                    const uint32_t m = __ballot_sync(0xffffffffu, lt);
+                    if (m) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&cnt_sh, __popc(m));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        const int slot = base + __popc(m & lt_mask);
+                        if (lt && slot < FC) G[slot] = (uint64_t)(w0 + (int64_t)u * HT + lane);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint64_t y = __shfl_xor_sync(0xffffffffu, mn, o);
+                mn = y < mn ? y : mn;
+                hl += __shfl_xor_sync(0xffffffffu, hl, o);
+            }
+            if (lane == 0) {
+                atomicMin(&min_sh, (unsigned long long)mn);
+                atomicAdd(&holes_sh, (unsigned long long)hl);
+            }
+            __syncthreads();
+            cnt = cnt_sh;
+            bmin = min_sh;
+            holes = (int64_t)holes_sh;
+            __syncthreads();
+            if (bmin == EMPTY) {  // only holes left: the column is zero
+                if (threadIdx.x == 0) S.bsize = 0;
                 __syncthreads();
-                const int cnt = cnt_sh;
-                const uint64_t bmin = min_sh;
-                __syncthreads();
-                if (cnt >= 1 && cnt <= FC) break;
-                if (cnt == 0 || q <= 1) { T = bmin + 1; break; }  // the smallest key alone
+                return false;
+            }
+            if (cnt >= 1 && cnt <= FC) break;
+            if (cnt > FC && T == bmin + 1) break;  // one key with more copies than fit
+            if (cnt == 0 || q <= 1) {
+                T = bmin + 1;  // the smallest key alone
+            } else {
                 q >>= 1;
-                T = G[q];
+                T = Sm[q];
             }
         }
-        // 3. move rows < T to the spare buffer (tile by tile: B is compacted in place)
-        int nlt = 0;
-        int64_t nge = 0;
-        constexpr int PER = 8;  // rows per thread per tile: one block scan per HT * PER rows
-        for (int64_t base = 0; base < bsz; base += (int64_t)HT * PER) {
-            const int64_t i0 = base + (int64_t)threadIdx.x * PER;
-            uint64_t k[PER];
-            int cl = 0, cg = 0;
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                k[q] = i0 + q < bsz ? B[i0 + q] : EMPTY;
-                if (i0 + q < bsz) { if (k[q] < T) ++cl; else ++cg; }
-            }
-            int tot;
-            const int packed = block_excl_scan(cl | (cg << 16), S.ws, &tot);  // all of the tile is read
-            int pl = nlt + (packed & 0xFFFF);
-            int64_t pg = nge + (packed >> 16);
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                if (i0 + q >= bsz) continue;
-                if (k[q] < T) { if (pl < FC) G[pl] = k[q]; ++pl; }
-                else B[pg++] = k[q];
-            }
-            nlt += tot & 0xFFFF;
-            nge += tot >> 16;
-        }
-        __syncthreads();
-        if (nlt > FC) {  // one key with more copies than fit (T = that key + 1): keep its parity only
+        HPROF_LAP(5);
+        if (cnt > FC) {  // every copy of bmin becomes a hole; its parity decides
+            for (int64_t i = threadIdx.x; i < bsz; i += HT)
+                if (B[i] == bmin) B[i] = EMPTY;
+            __syncthreads();
             if (threadIdx.x == 0) {
-                S.buf[S.cur][0] = T - 1;
-                S.fsize = (nlt & 1) ? 1 : 0;
-                S.bsize = nge;
+                S.buf[S.cur][0] = bmin;
+                S.fsize = cnt & 1;
                 S.Ks = T;
             }
             __syncthreads();
-            if (S.fsize) return true;
-            continue;
+            holes += cnt;
+        } else {
+            // gather the rows and leave holes
+            for (int i = threadIdx.x; i < cnt; i += HT) {
+                const int64_t pos = (int64_t)G[i];
+                G[i] = B[pos];
+                B[pos] = EMPTY;
+            }
+            holes += cnt;
+            int len = 1;
+            while (len < cnt) len <<= 1;
+            for (int i = cnt + threadIdx.x; i < len; i += HT) G[i] = EMPTY;
+            __syncthreads();
+            HPROF_LAP(6);
+            block_bitonic(G, len);
+            // keep the rows of odd multiplicity
+            uint64_t* F = S.buf[S.cur];
+            const int chunk = (cnt + HT - 1) / HT;
+            const int c0 = min(cnt, (int)threadIdx.x * chunk), c1 = min(cnt, c0 + chunk);
+            int keep = 0;
+            for (int i = c0; i < c1; ++i) {
+                if (i > 0 && G[i - 1] == G[i]) continue;
+                int e = i;
+                while (e + 1 < cnt && G[e + 1] == G[i]) ++e;
+                keep += ((e - i + 1) & 1);
+            }
+            int tk;
+            int pos = block_excl_scan(keep, S.ws, &tk);
+            for (int i = c0; i < c1; ++i) {
+                if (i > 0 && G[i - 1] == G[i]) continue;
+                int e = i;
+                while (e + 1 < cnt && G[e + 1] == G[i]) ++e;
+                if ((e - i + 1) & 1) F[pos++] = G[i];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                S.fsize = tk;
+                S.Ks = T;
+            }
+            __syncthreads();
         }
-        int len = 1;
-        while (len < nlt) len <<= 1;
-        for (int i = nlt + threadIdx.x; i < len; i += HT) G[i] = EMPTY;
-        __syncthreads();
-        block_bitonic(G, len);
-        // 4. keep the rows of odd multiplicity
-        uint64_t* F = S.buf[S.cur];
-        const int chunk = (nlt + HT - 1) / HT;
-        const int c0 = min(nlt, (int)threadIdx.x * chunk), c1 = min(nlt, c0 + chunk);
-        int keep = 0;
-        for (int i = c0; i < c1; ++i) {
-            if (i > 0 && G[i - 1] == G[i]) continue;
-            int e = i;
-            while (e + 1 < nlt && G[e + 1] == G[i]) ++e;
-            keep += ((e - i + 1) & 1);
+        if (holes == bsz) {
+            if (threadIdx.x == 0) S.bsize = 0;
+            __syncthreads();
+        } else if (2 * holes > bsz) {
+            heavy_compact_back(S, B);
         }
-        int tk;
-        int pos = block_excl_scan(keep, S.ws, &tk);
-        for (int i = c0; i < c1; ++i) {
-            if (i > 0 && G[i - 1] == G[i]) continue;
-            int e = i;
-            while (e + 1 < nlt && G[e + 1] == G[i]) ++e;
-            if ((e - i + 1) & 1) F[pos++] = G[i];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            S.fsize = tk;
-            S.bsize = nge;
-            S.Ks = T;
-        }
-        __syncthreads();
-        if (tk > 0) return true;
+        HPROF_LAP(7);
+        if (S.fsize > 0) return true;
     }
 }
 
@@ -766,6 +866,7 @@ template <int P>
 __device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x) {
     const int64_t n = c.R.n;
     for (int64_t base = n - 1; base >= 0; base -= HT) {
+        HPROF_T0();
         const int64_t w = base - (int64_t)threadIdx.x;
         bool ok = w >= 0;
 #pragma unroll
@@ -795,8 +896,11 @@ __device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, in
         __syncthreads();
         if (threadIdx.x == 0) S.bsize = bs + nge;
         __syncthreads();
+        HPROF_LAP(0);
         stage_sort(S, nlt);
+        HPROF_LAP(1);
         if (!heavy_merge_front(S, B, bcap, nlt)) return false;
+        HPROF_LAP(2);
     }
     return true;
 }
@@ -814,42 +918,97 @@ __device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_
     return true;
 }
 
-// W <- W + R_o where R_o = rows[0..len) is any multiset of rows (for example
-// the front and the unsorted back of a column finished by the block engine):
-// each chunk is sorted and its rows of even multiplicity cancel before the
-// chunk is added; rows repeated across chunks cancel in the front or later.
-__device__ bool heavy_add_multiset(HeavySmem& S, uint64_t* B, int64_t bcap, const uint64_t* rows, int64_t len) {
-    for (int64_t base = 0; base < len; base += HSTAGE) {
-        const int cnt = (int)min((int64_t)HSTAGE, len - base);
-        for (int i = threadIdx.x; i < cnt; i += HT) S.stage[i] = rows[base + i];
-        __syncthreads();
-        stage_sort(S, cnt);
-        // keep one row per run of odd length (chunk is at most HSTAGE = 2 * HT rows)
-        bool keep0 = false, keep1 = false;
-        const int i0 = threadIdx.x, i1 = threadIdx.x + HT;
-        uint64_t v0 = 0, v1 = 0;
-        if (i0 < cnt && (i0 == 0 || S.stage[i0 - 1] != S.stage[i0])) {
-            int e = i0;
-            while (e + 1 < cnt && S.stage[e + 1] == S.stage[i0]) ++e;
-            keep0 = ((e - i0 + 1) & 1) != 0;
-            v0 = S.stage[i0];
-        }
-        if (i1 < cnt && (S.stage[i1 - 1] != S.stage[i1])) {
-            int e = i1;
-            while (e + 1 < cnt && S.stage[e + 1] == S.stage[i1]) ++e;
-            keep1 = ((e - i1 + 1) & 1) != 0;
-            v1 = S.stage[i1];
-        }
-        // rows 0..HT-1 first, then HT..2HT-1, so the kept rows stay in order
-        int tot0, tot1;
-        const int pos0 = block_excl_scan((int)keep0, S.ws, &tot0);  // syncs: all reads are done
-        const int pos1 = block_excl_scan((int)keep1, S.ws, &tot1);
-        if (keep0) S.stage[pos0] = v0;
-        if (keep1) S.stage[tot0 + pos1] = v1;
-        __syncthreads();
-        if (!heavy_add_run(S, B, bcap, tot0 + tot1)) return false;
+// Sort stage[0..cnt) (cnt <= HSTAGE), keep one row of every run of odd
+// length (Z/2) and add the result to W.
+__device__ bool heavy_flush_stage(HeavySmem& S, uint64_t* B, int64_t bcap, int cnt) {
+    stage_sort(S, cnt);
+    bool keep0 = false, keep1 = false;
+    const int i0 = threadIdx.x, i1 = threadIdx.x + HT;
+    uint64_t v0 = 0, v1 = 0;
+    if (i0 < cnt && (i0 == 0 || S.stage[i0 - 1] != S.stage[i0])) {
+        int e = i0;
+        while (e + 1 < cnt && S.stage[e + 1] == S.stage[i0]) ++e;
+        keep0 = ((e - i0 + 1) & 1) != 0;
+        v0 = S.stage[i0];
     }
-    return true;
+    if (i1 < cnt && (S.stage[i1 - 1] != S.stage[i1])) {
+        int e = i1;
+        while (e + 1 < cnt && S.stage[e + 1] == S.stage[i1]) ++e;
+        keep1 = ((e - i1 + 1) & 1) != 0;
+        v1 = S.stage[i1];
+    }
+    // rows 0..HT-1 first, then HT..2HT-1, so the kept rows stay in order
+    int tot0, tot1;
+    const int pos0 = block_excl_scan((int)keep0, S.ws, &tot0);  // syncs: all reads are done
+    const int pos1 = block_excl_scan((int)keep1, S.ws, &tot1);
+    if (keep0) S.stage[pos0] = v0;
+    if (keep1) S.stage[tot0 + pos1] = v1;
+    __syncthreads();
+    return heavy_add_run(S, B, bcap, tot0 + tot1);
+}
+
+// W <- W + R_o where R_o = rows[0..len) is any multiset of rows (for example
+// the front and the unsorted back of a column finished by the block engine;
+// holes, EMPTY, are skipped).
+// Rows at or above the split go straight to the back; rows below it collect
+// in the stage, which is flushed (sorted, cancelled, merged) whenever the
+// next tile might not fit.  The next tile is loaded before the current one
+// is placed, so one memory latency per tile overlaps the block scan.
+__device__ bool heavy_add_multiset(HeavySmem& S, uint64_t* B, int64_t bcap, const uint64_t* rows, int64_t len) {
+    HPROF_T0();
+    if (threadIdx.x == 0) S.tp[8] += 1;
+    constexpr int PER = HSTAGE / HT;
+    uint64_t nk[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int64_t i = (int64_t)q * HT + threadIdx.x;
+        nk[q] = i < len ? rows[i] : EMPTY;
+    }
+    int sc = 0;  // rows in the stage
+    for (int64_t base = 0; base < len; base += HSTAGE) {
+        uint64_t k[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) k[q] = nk[q];
+        if (base + HSTAGE < len) {
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int64_t i = base + HSTAGE + (int64_t)q * HT + threadIdx.x;
+                nk[q] = i < len ? rows[i] : EMPTY;
+            }
+        }
+        const uint64_t Ks = S.Ks;
+        int cl = 0, cg = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            if (k[q] != EMPTY) {  // out of range, or a hole of a block-engine back
+                if (k[q] < Ks) ++cl; else ++cg;
+            }
+        }
+        int tot;
+        const int packed = block_excl_scan(cl | (cg << 16), S.ws, &tot);
+        const int nlt = tot & 0xFFFF, nge = tot >> 16;
+        if (sc + nlt > HSTAGE) {  // flushing may lower Ks: rows kept below the old split stay valid
+            if (!heavy_flush_stage(S, B, bcap, sc)) return false;
+            sc = 0;
+        }
+        const int64_t bs = S.bsize;
+        if (bs + nge > bcap) return false;
+        int pl = sc + (packed & 0xFFFF);
+        int64_t pg = bs + (packed >> 16);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            if (k[q] != EMPTY) {
+                if (k[q] < Ks) S.stage[pl++] = k[q]; else B[pg++] = k[q];
+            }
+        }
+        sc += nlt;
+        __syncthreads();
+        if (threadIdx.x == 0) S.bsize = bs + nge;
+        __syncthreads();
+    }
+    const bool ok = sc == 0 || heavy_flush_stage(S, B, bcap, sc);
+    HPROF_LAP(3);
+    return ok;
 }
 
 // Owner of pivot rk (see warp_owner); result in S.opos / S.ov / S.orank.
@@ -872,7 +1031,7 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
         int drop = -1;
         int tv[NT];
         {
-            decode_simplex<P + 1>(c.B, ct, n - 1, tv);
+            warp_decode_simplex<P + 1>(c.B, ct, n - 1, tv);
             bool eq = false;
             int pi = 0, pj = 0;
             if (lane < NPAIR) {

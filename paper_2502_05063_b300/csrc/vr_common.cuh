@@ -114,6 +114,30 @@ __device__ __forceinline__ void decode_simplex(const Binom& B, uint64_t c, int64
     }
 }
 
+// The same decoding by a whole (converged) warp: each vertex is found by a
+// 32-ary search (lane L tests lo + L * step; the tested values C(x, i+1) grow
+// with x, so the passing lanes form a prefix), two dependent table reads per
+// vertex for n <= 1024 instead of log2(n).  Every lane receives v.
+template <int Q>
+__device__ __forceinline__ void warp_decode_simplex(const Binom& B, uint64_t c, int64_t top, int* v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = Q; i >= 0; --i) {
+        int64_t lo = i, hi = top;  // C(lo, i+1) <= c holds throughout
+        while (lo < hi) {
+            const int64_t step = (hi - lo + 32) >> 5;  // ceil((hi - lo + 1) / 32)
+            const int64_t x = lo + (int64_t)lane * step;
+            const bool ok = x <= hi && B(x, i + 1) <= c;
+            const int L = 31 - __clz((int)__ballot_sync(0xffffffffu, ok));
+            lo += (int64_t)L * step;
+            hi = min(hi, lo + step - 1);
+        }
+        v[i] = (int)lo;
+        c -= B(lo, i + 1);
+        top = lo - 1;
+    }
+}
+
 // Diameter ranks: the distance matrix is replaced by the dense rank of each
 // entry among the distinct values {0} U {d(i,j)}, so that "diam(a) < diam(b)"
 // and "diam(a) == diam(b)" are integer comparisons; ranks map back to the
