@@ -28,12 +28,13 @@
 // Phase 1: one warp per column, at most 8 additions, all columns at once;
 // finished columns that needed additions keep their reduced form.  Phase 2:
 // one block per remaining column (the front/back engine of
-// reduce_device.cuh), state kept across rounds, budgets doubling; a column
+// reduce_device.cuh), state kept across rounds, at most 128 additions per
+// round so that finalized pivots reach waiting columns early; a column
 // whose pivot belongs to a column finished in phase 2 adds that column's
 // reduced form.  The first unfinished column can never be blocked, so every
-// round with enough budget makes progress; a stall with an overflowing first
-// column moves the remaining columns to larger buffers (VR_ERR_OOM if they
-// cannot grow).
+// round makes progress (it is finalized or gains its additions); a stall
+// with an overflowing first column moves the remaining columns to larger
+// buffers (VR_ERR_OOM if they cannot grow).
 //
 // Pivot lookup (the paper's two-layer store, Fig 5.10): first a device hash
 // of pivots found by this reduction, then the apparent pairs, which are not
@@ -164,7 +165,7 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
     const uint64_t self_key = c.cols[j];
     Simplex<P> s;
     load_col<P>(c, self_key, s);
-    if (threadIdx.x < 10) S.tp[threadIdx.x] = 0;
+    if (threadIdx.x < 20) S.tp[threadIdx.x] = 0;
     __syncthreads();
     uint32_t adds;
     bool ok = true;
@@ -197,6 +198,7 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
         ++n_look;
         if (!owned) break;  // pivot unknown: complete
         if (done >= budget) { st = ST_BUDGET; break; }
+        if (hs.prof && threadIdx.x == 0) S.tp[15] -= clock64();
         if (S.flag == 1) {
             const int64_t opos = S.opos;
             const uint32_t os = slot_of[opos];
@@ -221,6 +223,7 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
         ++adds;
         ++done;
         __syncthreads();
+        if (hs.prof && threadIdx.x == 0) S.tp[15] += clock64();
         t_add += clock64() - tc;
     }
     if (hs.prof && threadIdx.x == 0) {
@@ -233,12 +236,17 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
         atomicMax(hs.prof + 6, (unsigned long long)done);
         atomicMax(hs.prof + 7, (unsigned long long)(clock64() - t_resume));
         const long long tot = clock64() - t_resume;
-        if (tot > 4000000)
+        if (tot > 1500000 && done >= 100)
             printf("[vr] dim%d col %lld: %d adds %lld cycles: refill %lld lookup %lld add %lld | gen %lld sort %lld "
                    "merge %lld multiset %lld (%lld) | refill sample %lld count %lld compact %lld sort %lld (%lld) "
                    "back %lld front %d\n",
                    P, (long long)j, done, tot, t_ref, t_look, t_add, S.tp[0], S.tp[1], S.tp[2], S.tp[3], S.tp[8],
                    S.tp[4], S.tp[5], S.tp[6], S.tp[7], S.tp[9], (long long)S.bsize, S.fsize);
+        if (tot > 1500000 && done >= 100)
+            printf("[vr] dim%d col %lld: merge search+scan %lld place %lld swap+spill %lld | owner hash/decode %lld "
+                   "apparent scan %lld | add total %lld | t0 search %lld, merges %lld, mean a %lld b %lld\n",
+                   P, (long long)j, S.tp[10], S.tp[11], S.tp[12], S.tp[13], S.tp[14], S.tp[15], S.tp[16], S.tp[19],
+                   S.tp[17] / (S.tp[19] ? S.tp[19] : 1), S.tp[18] / (S.tp[19] ? S.tp[19] : 1));
     }
     if (!ok) st = ST_OVERFLOW;  // key holds the last consistent pivot, a valid bound
     for (int i = threadIdx.x; i < S.fsize && ok; i += HT) hs.F[slot * FC + i] = S.buf[S.cur][i];
@@ -301,8 +309,8 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         u = hs.p[8];
     }
     // Phase 2: one block per remaining column, state kept between rounds; the
-    // first unfinished column always finishes once its budget suffices (no
-    // earlier column can block it), so budgets double every round.
+    // first unfinished column can never be blocked by an earlier one, so it
+    // gains `budget` additions every round until it is finalized.
     int rounds = 0;
     if (u > 0) {
         const size_t smem = sizeof(HeavySmem);
@@ -322,6 +330,11 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));  // no slot: phase-1 columns
         k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
         int budget = 64;
+        // Columns are finalized between rounds only, so a round that runs as
+        // long as its longest column would keep columns it unblocks idle; a
+        // cap of 128 additions (about 1 ms) keeps rounds short.
+        constexpr int budget_cap = 128;
+        int64_t stalled_adds = 0;  // additions granted to the first column since a column was last finalized
         cudaEvent_t ev[2] = {nullptr, nullptr};
         if (h.prof) { VR_CUDA(cudaEventCreate(&ev[0])); VR_CUDA(cudaEventCreate(&ev[1])); }
         while (u > 0) {
@@ -352,7 +365,8 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
             uint32_t* t = U; U = Un; Un = t;
             const bool stalled = un == u;
             u = un;
-            if (stalled && budget >= (1 << 22)) throw Error{VR_ERR_INTERNAL};  // no column can need this many
+            stalled_adds = stalled ? stalled_adds + budget : 0;
+            if (stalled_adds > ((int64_t)1 << 24)) throw Error{VR_ERR_INTERNAL};  // no column can need this many
             if (stalled && first == ST_OVERFLOW) {
                 // the first column outgrew its back buffer: give the remaining
                 // columns the whole arena (they restart from scratch)
@@ -365,7 +379,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
                 VR_CUDA(cudaGetLastError());
             }
-            if (budget < (1 << 24)) budget *= 2;
+            if (budget < budget_cap) budget *= 2;
         }
         if (h.prof) {
             VR_CUDA(cudaEventDestroy(ev[0]));

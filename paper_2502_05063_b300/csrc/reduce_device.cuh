@@ -450,8 +450,8 @@ constexpr int FC = 4096;         // front capacity
 constexpr int FKEEP = FC - 1024; // front size kept after a spill
 constexpr int HSTAGE = 1024;     // rows generated or copied per pass (power of two >= HT)
 constexpr int REFILL = FC / 2;   // rows promoted from the back per refill (at most)
-static_assert(HSTAGE == 2 * HT, "a merge takes two run rows per thread");
-static_assert(FC < (1 << 16) && HSTAGE < (1 << 15), "merge positions are packed in 16 + 15 bits");
+static_assert(HSTAGE == 2 * HT, "a flushed stage holds two rows per thread");
+static_assert(HW <= 32, "block scans keep one total per warp in one warp");
 
 struct HeavyState {
     uint64_t* F;       // slots x FC, the front saved between rounds
@@ -471,7 +471,6 @@ __device__ unsigned long long g_heavy_counts[4];
 struct HeavySmem {
     uint64_t buf[2][FC];   // the front and its merge target, swapped after each merge
     uint64_t stage[HSTAGE];
-    uint32_t mq[HSTAGE];   // merge: per run row, its place in the front | cancellations before it | cancels
     int ws[HW + 1];
     uint32_t hist[256];
     uint64_t Ks;
@@ -483,12 +482,15 @@ struct HeavySmem {
     int ov[VR_MAX_DIM + 2];
     uint32_t orank;
     uint64_t sel;          // radix-select result
-    long long tp[10];      // VR_LOG only (thread 0): sub-phase cycles
+    long long tp[20];      // VR_LOG only (thread 0): sub-phase cycles
 };
 #define HPROF_T0() long long _hp_t = clock64()
 #define HPROF_LAP(i) do { if (threadIdx.x == 0) { long long _n = clock64(); S.tp[i] += _n - _hp_t; _hp_t = _n; } } while (0)
 
-// exclusive block scan of one int per thread; *total receives the sum
+// exclusive block scan of one int per thread; *total receives the sum.
+// Warp scans, one barrier to publish the warp totals, then every warp sums
+// the totals before it itself (no second scan stage); the trailing barrier
+// lets the next call reuse ws.
 __device__ __forceinline__ int block_excl_scan(int x, int* ws, int* total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int incl = x;
@@ -499,22 +501,16 @@ __device__ __forceinline__ int block_excl_scan(int x, int* ws, int* total) {
     }
     if (lane == 31) ws[wid] = incl;
     __syncthreads();
-    if (wid == 0) {
-        int t = lane < HW ? ws[lane] : 0;
-        int ti = t;
+    const int v = lane < HW ? ws[lane] : 0;
+    int before = lane < wid ? v : 0, all = v;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, ti, o);
-            if (lane >= o) ti += y;
-        }
-        if (lane < HW) ws[lane] = ti - t;
-        if (lane == HW - 1) ws[HW] = ti;
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
     }
+    *total = all;
     __syncthreads();
-    const int r = ws[wid] + incl - x;
-    *total = ws[HW];
-    __syncthreads();
-    return r;
+    return before + incl - x;
 }
 
 __device__ void block_bitonic(uint64_t* a, int len) {
@@ -581,64 +577,68 @@ __device__ bool heavy_append(HeavySmem& S, uint64_t* B, int64_t bcap, const uint
     return true;
 }
 
+// Lower bounds of x0 and x1 in a[0..len), searched in lockstep (branch-free
+// halving, so the two dependent load chains overlap).
+__device__ __forceinline__ void lower_bound_sm2(const uint64_t* a, int len, uint64_t x0, uint64_t x1, int& r0,
+                                                int& r1) {
+    if (len == 0) { r0 = r1 = 0; return; }
+    int b0 = 0, b1 = 0, n = len;
+    while (n > 1) {
+        const int h = n >> 1;
+        b0 = a[b0 + h] < x0 ? b0 + h : b0;
+        b1 = a[b1 + h] < x1 ? b1 + h : b1;
+        n -= h;
+    }
+    r0 = b0 + (a[b0] < x0);
+    r1 = b1 + (a[b1] < x1);
+}
+
 // front <- front XOR stage[0..b), stage sorted, unique and entirely below Ks.
-// Merge by position: run row k, with lower bound q_k in the front and E_k
-// earlier run rows that cancel a front row, lands at q_k + k - 2 E_k (or
-// cancels F[q_k]); front row i lands at i + r_i - 2 E(i), r_i run rows below
-// it and E(i) cancellations before it, which each thread reads off the
-// sorted q's for its chunk of the front.
+// Merge path by front chunks: thread t owns the front rows F[f0, f1) and the
+// run rows in [F[f0], F[f1]) (found by searching the short run, not the
+// front), merges them with equal rows cancelling, and writes at the offset
+// a block scan of the per-thread output counts gives.
 __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
     if (b == 0) return true;
     const uint64_t* run = S.stage;
     const uint64_t* F = S.buf[S.cur];
     uint64_t* F2 = S.buf[S.cur ^ 1];
     const int a = S.fsize;
-    // 1. run rows 2t and 2t+1 (b <= HSTAGE = 2 HT)
-    const int k0 = 2 * (int)threadIdx.x;
-    int q0 = 0, q1 = 0;
-    bool e0 = false, e1 = false;
-    if (k0 < b) {
-        q0 = lower_bound_sm(F, a, run[k0]);
-        e0 = q0 < a && F[q0] == run[k0];
-    }
-    if (k0 + 1 < b) {
-        q1 = lower_bound_sm(F, a, run[k0 + 1]);
-        e1 = q1 < a && F[q1] == run[k0 + 1];
-    }
-    int etot;
-    const int ex = block_excl_scan((int)e0 + (int)e1, S.ws, &etot);
-    if (k0 < b) {
-        S.mq[k0] = (uint32_t)q0 | ((uint32_t)ex << 16) | (e0 ? 0x80000000u : 0u);
-        if (!e0) F2[q0 + k0 - 2 * ex] = run[k0];
-    }
-    if (k0 + 1 < b) {
-        const int ex1 = ex + (int)e0;
-        S.mq[k0 + 1] = (uint32_t)q1 | ((uint32_t)ex1 << 16) | (e1 ? 0x80000000u : 0u);
-        if (!e1) F2[q1 + k0 + 1 - 2 * ex1] = run[k0 + 1];
-    }
-    __syncthreads();
-    // 2. the front, a contiguous chunk per thread
+    HPROF_T0();
     const int chunk = (a + HT - 1) / HT;
     const int f0 = min(a, (int)threadIdx.x * chunk), f1 = min(a, f0 + chunk);
-    if (f0 < f1) {
-        int lo = 0, hi = b;  // first run row with q >= f0
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((int)(S.mq[mid] & 0xFFFFu) < f0) lo = mid + 1; else hi = mid;
-        }
-        int k = lo;
-        int E = k < b ? (int)((S.mq[k] >> 16) & 0x7FFFu) : etot;
-        for (int i = f0; i < f1; ++i) {
-            uint32_t m;
-            while (k < b && (int)((m = S.mq[k]) & 0xFFFFu) < i) { E += (int)(m >> 31); ++k; }
-            int k2 = k;
-            bool canc = false;
-            while (k2 < b && (int)((m = S.mq[k2]) & 0xFFFFu) == i) { canc = canc || (m >> 31); ++k2; }
-            if (!canc) F2[i + k2 - 2 * E] = F[i];
+    const uint64_t x0 = threadIdx.x == 0 ? 0 : (f0 < a ? F[f0] : EMPTY);
+    const uint64_t x1 = f1 < a ? F[f1] : EMPTY;
+    int r0, r1;
+    lower_bound_sm2(run, b, x0, x1, r0, r1);
+    int canc = 0;
+    {
+        int i = f0, k = r0;
+        while (i < f1 && k < r1) {
+            const uint64_t x = F[i], y = run[k];
+            i += x <= y;
+            k += y <= x;
+            canc += x == y;
         }
     }
+    const int cnt = (f1 - f0) + (r1 - r0) - 2 * canc;  // rows this thread writes
+    if (threadIdx.x == 0) { S.tp[16] += clock64() - _hp_t; S.tp[17] += a; S.tp[18] += b; S.tp[19] += 1; }
+    int na;
+    int pos = block_excl_scan(cnt, S.ws, &na);
+    HPROF_LAP(10);
+    {
+        int i = f0, k = r0;
+        while (i < f1 && k < r1) {
+            const uint64_t x = F[i], y = run[k];
+            if (x < y) { F2[pos++] = x; ++i; }
+            else if (y < x) { F2[pos++] = y; ++k; }
+            else { ++i; ++k; }
+        }
+        while (i < f1) F2[pos++] = F[i++];
+        while (k < r1) F2[pos++] = run[k++];
+    }
     __syncthreads();
-    int na = a + b - 2 * etot;
+    HPROF_LAP(11);
     if (threadIdx.x == 0) S.cur ^= 1;
     __syncthreads();
     if (na > FKEEP) {  // spill the top of the front to B and lower the split
@@ -648,6 +648,7 @@ __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b
     }
     if (threadIdx.x == 0) S.fsize = na;
     __syncthreads();
+    HPROF_LAP(12);
     return true;
 }
 
@@ -1020,6 +1021,7 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
     const int64_t n = c.R.n;
     const uint32_t rt = (uint32_t)(rk >> c.rcb);
     const uint64_t ct = c.rcmask - (rk & c.rcmask);
+    HPROF_T0();
     // a row has at most one owner: warp 1 probes the hash of finished columns
     // while warp 0 prepares the apparent-pair test
     if (wid == 1) {
@@ -1058,6 +1060,7 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
         }
     }
     __syncthreads();
+    HPROF_LAP(13);
     if (S.opos >= 0) {  // the pivot of a finished column
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1083,7 +1086,9 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
             for (int q = 0; q <= P; ++q) ok = ok && (c.R(ov[q], w) <= rt);
             older = older || ok;
         }
-        return !__syncthreads_or(older);
+        const bool r = !__syncthreads_or(older);
+        HPROF_LAP(14);
+        return r;
     }
     return false;
 }
