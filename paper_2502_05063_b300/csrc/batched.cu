@@ -552,18 +552,21 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
                 if (++col_adds > (1ull << 22)) { ok = false; break; }  // far beyond any column: flag the cloud
                 if (S.fsize == 0 && !heavy_refill(S, back, 32 + TRI_BITS)) { key = EMPTY; break; }
                 key = S.buf[S.cur][0];
-                if (!heavy_owner<1>(c, S, key, self_key)) break;
-                Simplex<1> o;
-                if (S.flag == 1 && c.rc_len[S.opos]) {
-                    ok = heavy_add_stored(c, S, back, BACKCAP, S.opos);
-                } else {
-                    if (S.flag == 1) {
-                        load_col<1>(c, cols[S.opos], o);
+                const int kind = heavy_owner_probe<1>(c, S, key, self_key);
+                if (kind == 0) break;
+                if (kind == 1) {
+                    const int64_t opos = S.opos;
+                    if (c.rc_len[opos]) {
+                        ok = heavy_add_stored(c, S, back, BACKCAP, opos);
                     } else {
-                        o.v[0] = S.ov[0]; o.v[1] = S.ov[1];
-                        o.r = S.orank;
+                        Simplex<1> o;
+                        load_col<1>(c, cols[opos], o);
+                        ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, o);
                     }
-                    ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, o);
+                } else {
+                    const int r = heavy_apparent_add<1>(c, S, back, BACKCAP);
+                    if (r < 0) break;  // the pivot has no owner: the column is complete
+                    ok = r > 0;
                 }
                 ++adds;
                 __syncthreads();

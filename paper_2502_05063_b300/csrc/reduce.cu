@@ -192,14 +192,18 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
         long long tb = clock64();
         t_ref += tb - ta;
         key = S.buf[S.cur][0];
-        const bool owned = heavy_owner<P>(c, S, key, self_key);
+        const int kind = heavy_owner_probe<P>(c, S, key, self_key);
         long long tc = clock64();
         t_look += tc - tb;
         ++n_look;
-        if (!owned) break;  // pivot unknown: complete
-        if (done >= budget) { st = ST_BUDGET; break; }
+        if (kind == 0) break;  // pivot unknown: complete
+        if (done >= budget) {
+            if (kind == 2 && !heavy_apparent_check<P>(c, S)) break;  // no owner after all: complete
+            st = ST_BUDGET;
+            break;
+        }
         if (hs.prof && threadIdx.x == 0) S.tp[15] -= clock64();
-        if (S.flag == 1) {
+        if (kind == 1) {
             const int64_t opos = S.opos;
             const uint32_t os = slot_of[opos];
             if (os != 0xFFFFFFFFu && hs.init[os] && hs.adds[os] > 0) {
@@ -214,11 +218,12 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
                 ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, o);
             }
         } else {
-            Simplex<P> o;
-#pragma unroll
-            for (int q = 0; q <= P; ++q) o.v[q] = S.ov[q];
-            o.r = S.orank;
-            ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, o);
+            const int r = heavy_apparent_add<P>(c, S, B, hs.bcap);
+            if (r < 0) {  // s' is not apparent: the pivot has no owner, the column is complete
+                if (hs.prof && threadIdx.x == 0) S.tp[15] += clock64();
+                break;
+            }
+            ok = r > 0;
         }
         ++adds;
         ++done;

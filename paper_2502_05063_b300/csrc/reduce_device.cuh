@@ -452,6 +452,7 @@ constexpr int HSTAGE = 1024;     // rows generated or copied per pass (power of 
 constexpr int REFILL = FC / 2;   // rows promoted from the back per refill (at most)
 static_assert(HSTAGE == 2 * HT, "a flushed stage holds two rows per thread");
 static_assert(HW <= 32, "block scans keep one total per warp in one warp");
+static_assert(FC < (1 << 16) && HSTAGE < (1 << 16), "merge splits pack two 16-bit indices");
 
 struct HeavyState {
     uint64_t* F;       // slots x FC, the front saved between rounds
@@ -471,6 +472,8 @@ __device__ unsigned long long g_heavy_counts[4];
 struct HeavySmem {
     uint64_t buf[2][FC];   // the front and its merge target, swapped after each merge
     uint64_t stage[HSTAGE];
+    uint32_t msplit[HT];               // merge: (front index << 16) | run index at each thread's diagonal
+    uint32_t eqbits[HSTAGE / 32];      // merge: run rows that cancel a front row
     int ws[HW + 1];
     uint32_t hist[256];
     uint64_t Ks;
@@ -577,27 +580,17 @@ __device__ bool heavy_append(HeavySmem& S, uint64_t* B, int64_t bcap, const uint
     return true;
 }
 
-// Lower bounds of x0 and x1 in a[0..len), searched in lockstep (branch-free
-// halving, so the two dependent load chains overlap).
-__device__ __forceinline__ void lower_bound_sm2(const uint64_t* a, int len, uint64_t x0, uint64_t x1, int& r0,
-                                                int& r1) {
-    if (len == 0) { r0 = r1 = 0; return; }
-    int b0 = 0, b1 = 0, n = len;
-    while (n > 1) {
-        const int h = n >> 1;
-        b0 = a[b0 + h] < x0 ? b0 + h : b0;
-        b1 = a[b1 + h] < x1 ? b1 + h : b1;
-        n -= h;
-    }
-    r0 = b0 + (a[b0] < x0);
-    r1 = b1 + (a[b1] < x1);
-}
-
 // front <- front XOR stage[0..b), stage sorted, unique and entirely below Ks.
-// Merge path by front chunks: thread t owns the front rows F[f0, f1) and the
-// run rows in [F[f0], F[f1]) (found by searching the short run, not the
-// front), merges them with equal rows cancelling, and writes at the offset
-// a block scan of the per-thread output counts gives.
+// Merge path: the merged sequence (a + b rows before cancellation) is cut
+// into equal diagonals, one per thread, so rows that cluster in one gap of
+// the front still spread over the threads.  Each thread finds the split of
+// its diagonal by a binary search no longer than log2(b) (equal rows ordered
+// front first; a boundary between a front row and an equal run row moves
+// before the front row, so every cancelling pair stays in one thread's
+// range) and reads the end of its range from the next thread.  Cancelled
+// run rows are marked in a bit mask, so a thread's output offset is its
+// diagonal minus twice the cancelled run rows before its range, without a
+// block scan.
 __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
     if (b == 0) return true;
     const uint64_t* run = S.stage;
@@ -605,49 +598,65 @@ __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b
     uint64_t* F2 = S.buf[S.cur ^ 1];
     const int a = S.fsize;
     HPROF_T0();
-    const int chunk = (a + HT - 1) / HT;
-    const int f0 = min(a, (int)threadIdx.x * chunk), f1 = min(a, f0 + chunk);
-    const uint64_t x0 = threadIdx.x == 0 ? 0 : (f0 < a ? F[f0] : EMPTY);
-    const uint64_t x1 = f1 < a ? F[f1] : EMPTY;
-    int r0, r1;
-    lower_bound_sm2(run, b, x0, x1, r0, r1);
-    int canc = 0;
+    const int tot = a + b;
+    const int per = (tot + HT - 1) / HT;
+    const int d = min(tot, (int)threadIdx.x * per);
+    int lo = max(0, d - a), hi = min(d, b);
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (run[m] < F[d - m - 1]) lo = m + 1; else hi = m;
+    }
+    const int k0 = lo;
+    int i0 = d - lo;
+    if (i0 > 0 && k0 < b && F[i0 - 1] == run[k0]) --i0;
+    S.msplit[threadIdx.x] = ((uint32_t)i0 << 16) | (uint32_t)k0;
+    if (threadIdx.x < HSTAGE / 32) S.eqbits[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t nx = threadIdx.x + 1 < HT ? S.msplit[threadIdx.x + 1] : (((uint32_t)a << 16) | (uint32_t)b);
+    const int i1 = (int)(nx >> 16), k1 = (int)(nx & 0xFFFFu);
     {
-        int i = f0, k = r0;
-        while (i < f1 && k < r1) {
+        int i = i0, k = k0;
+        while (i < i1 && k < k1) {
             const uint64_t x = F[i], y = run[k];
+            if (x == y) atomicOr(&S.eqbits[k >> 5], 1u << (k & 31));
             i += x <= y;
             k += y <= x;
-            canc += x == y;
         }
     }
-    const int cnt = (f1 - f0) + (r1 - r0) - 2 * canc;  // rows this thread writes
     if (threadIdx.x == 0) { S.tp[16] += clock64() - _hp_t; S.tp[17] += a; S.tp[18] += b; S.tp[19] += 1; }
-    int na;
-    int pos = block_excl_scan(cnt, S.ws, &na);
+    __syncthreads();
+    int eb = 0, et = 0;
+    for (int w = 0; w < ((b + 31) >> 5); ++w) {
+        const uint32_t m = S.eqbits[w];
+        const int base = w << 5;
+        et += __popc(m);
+        eb += base + 32 <= k0 ? __popc(m) : (base < k0 ? __popc(m & ((1u << (k0 - base)) - 1u)) : 0);
+    }
+    const int na = tot - 2 * et;
     HPROF_LAP(10);
+    if (threadIdx.x == 0) {  // every read of cur and fsize happened before the last barrier
+        S.cur ^= 1;
+        S.fsize = min(na, FKEEP);
+    }
     {
-        int i = f0, k = r0;
-        while (i < f1 && k < r1) {
+        int pos = i0 + k0 - 2 * eb;
+        int i = i0, k = k0;
+        while (i < i1 && k < k1) {
             const uint64_t x = F[i], y = run[k];
             if (x < y) { F2[pos++] = x; ++i; }
             else if (y < x) { F2[pos++] = y; ++k; }
             else { ++i; ++k; }
         }
-        while (i < f1) F2[pos++] = F[i++];
-        while (k < r1) F2[pos++] = run[k++];
+        while (i < i1) F2[pos++] = F[i++];
+        while (k < k1) F2[pos++] = run[k++];
     }
     __syncthreads();
     HPROF_LAP(11);
-    if (threadIdx.x == 0) S.cur ^= 1;
-    __syncthreads();
     if (na > FKEEP) {  // spill the top of the front to B and lower the split
-        if (!heavy_append(S, B, bcap, S.buf[S.cur] + FKEEP, na - FKEEP)) return false;
-        if (threadIdx.x == 0) S.Ks = S.buf[S.cur][FKEEP];
-        na = FKEEP;
+        if (!heavy_append(S, B, bcap, F2 + FKEEP, na - FKEEP)) return false;
+        if (threadIdx.x == 0) S.Ks = F2[FKEEP];
+        __syncthreads();
     }
-    if (threadIdx.x == 0) S.fsize = na;
-    __syncthreads();
     HPROF_LAP(12);
     return true;
 }
@@ -860,50 +869,66 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
     }
 }
 
-// W <- W + D_x for the p-simplex x (vertices ascending, diameter rank xr):
-// rows at or above the split go straight to B, only the few below it are
-// sorted and merged into the front.
+// Place one pass of generated rows (thread t holds `key` if `ok`): rows at
+// or above the split go straight to B, the few below it are sorted and
+// merged into the front.
+__device__ bool heavy_cob_place(HeavySmem& S, uint64_t* B, int64_t bcap, bool ok, uint64_t key) {
+    HPROF_T0();
+    const int64_t bs = S.bsize;  // read before the scan's barriers, rewritten after them
+    const bool lt = ok && key < S.Ks;
+    const bool ge = ok && !lt;
+    int tot;
+    const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
+    const int nlt = tot & 0xFFFF, nge = tot >> 16;
+    if (bs + nge > bcap) return false;
+    if (ge) B[bs + (packed >> 16)] = key;
+    if (lt) S.stage[packed & 0xFFFF] = key;
+    if (threadIdx.x == 0) {
+        S.bsize = bs + nge;
+        atomicAdd(&g_heavy_counts[1], (unsigned long long)nlt);
+        atomicAdd(&g_heavy_counts[2], (unsigned long long)nge);
+        atomicAdd(&g_heavy_counts[3], 1ull);
+    }
+    __syncthreads();
+    HPROF_LAP(0);
+    stage_sort(S, nlt);
+    HPROF_LAP(1);
+    if (!heavy_merge_front(S, B, bcap, nlt)) return false;
+    HPROF_LAP(2);
+    return true;
+}
+
+// Row key of x + {w} for the thread's w, if w is no vertex of x and the
+// cofacet is within the threshold.
 template <int P>
-__device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x) {
-    const int64_t n = c.R.n;
-    for (int64_t base = n - 1; base >= 0; base -= HT) {
-        HPROF_T0();
-        const int64_t w = base - (int64_t)threadIdx.x;
-        bool ok = w >= 0;
+__device__ __forceinline__ bool cob_row(const Ctx& c, const Simplex<P>& x, int64_t w, uint64_t& key) {
+    bool ok = w >= 0;
 #pragma unroll
-        for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
-        uint32_t rt = x.r;
+    for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
+    if (!ok) return false;
+    uint32_t rt = x.r;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
+    if (rt > c.thr) return false;
+    key = row_key<P>(c, x, w, rt);
+    return true;
+}
+
+// W <- W + D_x for the p-simplex x (vertices ascending, diameter rank x.r),
+// HT vertices w per pass from the top.
+template <int P>
+__device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x,
+                                     int64_t top) {
+    for (int64_t base = top; base >= 0; base -= HT) {
         uint64_t key = EMPTY;
-        if (ok) {
-#pragma unroll
-            for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
-            ok = rt <= c.thr;
-            if (ok) key = row_key<P>(c, x, w, rt);
-        }
-        const bool lt = ok && key < S.Ks;
-        const bool ge = ok && !lt;
-        int tot;
-        const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
-        const int nlt = tot & 0xFFFF, nge = tot >> 16;
-        if (threadIdx.x == 0) {
-            atomicAdd(&g_heavy_counts[1], (unsigned long long)nlt);
-            atomicAdd(&g_heavy_counts[2], (unsigned long long)nge);
-            atomicAdd(&g_heavy_counts[3], 1ull);
-        }
-        const int64_t bs = S.bsize;
-        if (bs + nge > bcap) return false;
-        if (ge) B[bs + (packed >> 16)] = key;
-        if (lt) S.stage[packed & 0xFFFF] = key;
-        __syncthreads();
-        if (threadIdx.x == 0) S.bsize = bs + nge;
-        __syncthreads();
-        HPROF_LAP(0);
-        stage_sort(S, nlt);
-        HPROF_LAP(1);
-        if (!heavy_merge_front(S, B, bcap, nlt)) return false;
-        HPROF_LAP(2);
+        const bool ok = cob_row<P>(c, x, base - (int64_t)threadIdx.x, key);
+        if (!heavy_cob_place(S, B, bcap, ok, key)) return false;
     }
     return true;
+}
+template <int P>
+__device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x) {
+    return heavy_add_coboundary<P>(c, S, B, bcap, x, c.R.n - 1);
 }
 
 // W <- W + R_o where R_o is a stored reduced column (sorted, unique).
@@ -1012,9 +1037,14 @@ __device__ bool heavy_add_multiset(HeavySmem& S, uint64_t* B, int64_t bcap, cons
     return ok;
 }
 
-// Owner of pivot rk (see warp_owner); result in S.opos / S.ov / S.orank.
+// Owner probe for pivot row rk: 1 = the pivot of a finished column (in
+// S.opos), 2 = a candidate apparent owner s' (Def 5.3.4: the facet left by
+// dropping the largest vertex whose removal keeps the diameter; S.ov[0..P],
+// the dropped vertex in S.ov[P+1], the diameter rank in S.orank), 0 = none.
+// A row has at most one owner: warp 1 probes the hash of finished columns
+// while warp 0 decodes the pivot and finds the dropped vertex.
 template <int P>
-__device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t self_key) {
+__device__ int heavy_owner_probe(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t self_key) {
     constexpr int NT = P + 2;
     constexpr int NPAIR = NT * (NT - 1) / 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1022,77 +1052,105 @@ __device__ bool heavy_owner(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t se
     const uint32_t rt = (uint32_t)(rk >> c.rcb);
     const uint64_t ct = c.rcmask - (rk & c.rcmask);
     HPROF_T0();
-    // a row has at most one owner: warp 1 probes the hash of finished columns
-    // while warp 0 prepares the apparent-pair test
     if (wid == 1) {
         const int64_t hp = warp_hash_find(c, ct);
-        if (lane == 0) S.opos = hp;
+        if (lane == 0) {
+            S.opos = hp;
+            if (hp >= 0 && !(c.cols[hp] < self_key)) atomicExch(c.err, DEV_INTERNAL);  // owners come earlier
+        }
     }
     if (wid == 0) {
-        int flag = 0;  // 2 = candidate apparent owner, 0 = none
         int drop = -1;
         int tv[NT];
-        {
-            warp_decode_simplex<P + 1>(c.B, ct, n - 1, tv);
-            bool eq = false;
-            int pi = 0, pj = 0;
-            if (lane < NPAIR) {
-                int k = lane;
-                pi = 1;
-                while (k >= pi) { k -= pi; ++pi; }
-                pj = k;
-                eq = c.R(tv[pi], tv[pj]) == rt;
-            }
-#pragma unroll
-            for (int m = NT - 1; m >= 0; --m)
-                if (drop < 0 && __ballot_sync(0xffffffffu, eq && pi != m && pj != m)) drop = m;
-            if (drop >= 0) flag = 2;
+        warp_decode_simplex<P + 1>(c.B, ct, n - 1, tv);
+        bool eq = false;
+        int pi = 0, pj = 0;
+        if (lane < NPAIR) {
+            int k = lane;
+            pi = 1;
+            while (k >= pi) { k -= pi; ++pi; }
+            pj = k;
+            eq = c.R(tv[pi], tv[pj]) == rt;
         }
+#pragma unroll
+        for (int m = NT - 1; m >= 0; --m)
+            if (drop < 0 && __ballot_sync(0xffffffffu, eq && pi != m && pj != m)) drop = m;
         if (lane == 0) {
-            S.flag = flag;
-            if (flag == 2) {
+            S.flag = drop >= 0 ? 2 : 0;
+            if (drop >= 0) {
                 int k = 0;
                 for (int q = 0; q < NT; ++q)
                     if (q != drop) S.ov[k++] = tv[q];
-                S.ov[P + 1] = tv[drop];  // the dropped vertex
+                S.ov[P + 1] = tv[drop];
                 S.orank = rt;
             }
         }
     }
     __syncthreads();
     HPROF_LAP(13);
-    if (S.opos >= 0) {  // the pivot of a finished column
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            S.flag = 1;
-            if (!(c.cols[S.opos] < self_key)) atomicExch(c.err, DEV_INTERNAL);
-        }
-        __syncthreads();
-        return true;
-    }
-    if (S.flag == 2) {
-        // apparent iff no vertex w above the dropped one keeps the diameter of s'
-        int ov[P + 1];
-#pragma unroll
-        for (int q = 0; q <= P; ++q) ov[q] = S.ov[q];
-        const int64_t wd = S.ov[P + 1];
-        bool older = false;
-        for (int64_t base = n - 1; base > wd; base -= HT) {
-            const int64_t w = base - (int64_t)threadIdx.x;
-            bool ok = w > wd;
-#pragma unroll
-            for (int q = 0; q <= P; ++q) ok = ok && (w != ov[q]);
-#pragma unroll
-            for (int q = 0; q <= P; ++q) ok = ok && (c.R(ov[q], w) <= rt);
-            older = older || ok;
-        }
-        const bool r = !__syncthreads_or(older);
-        HPROF_LAP(14);
-        return r;
-    }
-    return false;
+    return S.opos >= 0 ? 1 : S.flag;
 }
 
+// For a probe that returned 2: whether s' owns the pivot, i.e. no vertex w
+// above the dropped one keeps the diameter of s' (s' has no older cofacet).
+template <int P>
+__device__ bool heavy_apparent_check(const Ctx& c, HeavySmem& S) {
+    const int64_t n = c.R.n;
+    int ov[P + 1];
+#pragma unroll
+    for (int q = 0; q <= P; ++q) ov[q] = S.ov[q];
+    const int64_t wd = S.ov[P + 1];
+    const uint32_t rt = S.orank;
+    bool older = false;
+    for (int64_t base = n - 1; base > wd; base -= HT) {
+        const int64_t w = base - (int64_t)threadIdx.x;
+        bool ok = w > wd;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (w != ov[q]);
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (c.R(ov[q], w) <= rt);
+        older = older || ok;
+    }
+    return !__syncthreads_or(older);
+}
+
+// For a probe that returned 2: if s' owns the pivot, W <- W + D_{s'} and 1;
+// -1 if it does not (the pivot has no owner); 0 if B overflowed.  When one
+// pass of HT vertices covers every w above the dropped vertex, the ownership
+// test and the first pass of D_{s'} share their rank reads: each thread's
+// w is an older cofacet of s' exactly when its diameter stays at s''s.
+template <int P>
+__device__ int heavy_apparent_add(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap) {
+    const int64_t n = c.R.n;
+    Simplex<P> o;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) o.v[q] = S.ov[q];
+    o.r = S.orank;
+    const int64_t wd = S.ov[P + 1];
+    if (wd < n - 1 - HT) {
+        if (!heavy_apparent_check<P>(c, S)) return -1;
+        return heavy_add_coboundary<P>(c, S, B, bcap, o) ? 1 : 0;
+    }
+    HPROF_T0();
+    const int64_t w = n - 1 - (int64_t)threadIdx.x;
+    bool ok = w >= 0, older = false;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) ok = ok && (w != o.v[q]);
+    uint64_t key = EMPTY;
+    if (ok) {
+        uint32_t mx = 0;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) mx = max(mx, c.R(o.v[q], w));
+        older = w > wd && mx <= o.r;
+        const uint32_t rt = max(o.r, mx);
+        ok = rt <= c.thr;
+        if (ok) key = row_key<P>(c, o, w, rt);
+    }
+    if (__syncthreads_or(older)) return -1;
+    HPROF_LAP(14);
+    if (!heavy_cob_place(S, B, bcap, ok, key)) return 0;
+    return heavy_add_coboundary<P>(c, S, B, bcap, o, n - 1 - HT) ? 1 : 0;
+}
 
 }  // namespace
 }  // namespace vr
