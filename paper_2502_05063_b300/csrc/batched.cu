@@ -123,17 +123,17 @@ __device__ __forceinline__ bool rec_less(const PairRec& x, const PairRec& y) {
     return x.birth_cidx < y.birth_cidx;
 }
 
-// block bitonic sort of records (len a power of two, padded by the caller)
+// block bitonic sort of records (len a power of two, padded by the caller),
+// one compare pair per thread and step as in block_bitonic
 __device__ void block_sort_recs(PairRec* a, int len) {
+    const int half = len >> 1;
     for (int k = 2; k <= len; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < len; i += HT) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    PairRec x = a[i], y = a[ixj];
-                    const bool up = (i & k) == 0;
-                    if (rec_less(y, x) == up) { a[i] = y; a[ixj] = x; }
-                }
+            for (int p = threadIdx.x; p < half; p += HT) {
+                const int i = 2 * p - (p & (j - 1));
+                const PairRec x = a[i], y = a[i + j];
+                const bool up = (i & k) == 0;
+                if (rec_less(y, x) == up) { a[i] = y; a[i + j] = x; }
             }
             __syncthreads();
         }

@@ -516,15 +516,17 @@ __device__ __forceinline__ int block_excl_scan(int x, int* ws, int* total) {
     return before + incl - x;
 }
 
+// Bitonic sort of a[0..len), len a power of two.  Each thread takes compare
+// pairs, not elements: pair p of a stage with distance j joins i = 2p - (p mod
+// j) and i + j, so no lane idles on the upper half of a pair.
 __device__ void block_bitonic(uint64_t* a, int len) {
+    const int half = len >> 1;
     for (int k = 2; k <= len; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < len; i += HT) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    uint64_t x = a[i], y = a[ixj];
-                    if ((x > y) == ((i & k) == 0)) { a[i] = y; a[ixj] = x; }
-                }
+            for (int p = threadIdx.x; p < half; p += HT) {
+                const int i = 2 * p - (p & (j - 1));
+                const uint64_t x = a[i], y = a[i + j];
+                if ((x > y) == ((i & k) == 0)) { a[i] = y; a[i + j] = x; }
             }
             __syncthreads();
         }

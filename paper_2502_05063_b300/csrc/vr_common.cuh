@@ -114,23 +114,73 @@ __device__ __forceinline__ void decode_simplex(const Binom& B, uint64_t c, int64
     }
 }
 
-// The same decoding by a whole (converged) warp: each vertex is found by a
-// 32-ary search (lane L tests lo + L * step; the tested values C(x, i+1) grow
-// with x, so the passing lanes form a prefix), two dependent table reads per
-// vertex for n <= 1024 instead of log2(n).  Every lane receives v.
+// Largest v in [lo, hi] with C(v, k) <= c (C(lo, k) <= c given), for k <= 4,
+// from a closed-form estimate: C(v,2) <= c  <=>  v <= (1 + sqrt(1 + 8c)) / 2,
+// and C(v,3) ~ (v-1)^3 / 6, C(v,4) ~ (v-1.5)^4 / 24 within one of the float
+// root.  C(x, k) and C(x+1, k) are read together, so an exact estimate costs
+// one table round trip; otherwise a few checked steps correct it.  Returns
+// false if they run out (the caller then searches); *cv receives C(v, k).
+__device__ __forceinline__ bool binom_root(const Binom& B, uint64_t c, int k, int64_t lo, int64_t hi, int64_t& v,
+                                           uint64_t& cv) {
+    if (k == 1) {  // C(v,1) = v
+        v = c < (uint64_t)hi ? (int64_t)c : hi;
+        v = v < lo ? lo : v;
+        cv = (uint64_t)v;
+        return true;
+    }
+    const float fc = (float)c;
+    float est;
+    if (k == 2) est = 0.5f * (1.0f + sqrtf(1.0f + 8.0f * fc));
+    else if (k == 3) est = cbrtf(6.0f * fc) + 1.0f;
+    else est = powf(24.0f * fc, 0.25f) + 1.5f;
+    int64_t x = (int64_t)est;
+    x = x < lo ? lo : (x > hi ? hi : x);
+    uint64_t b0 = B(x, k), b1 = x < hi ? B(x + 1, k) : ~0ull;
+    for (int s = 0; s < 6; ++s) {
+        if (b0 > c && x > lo) {  // too high
+            --x;
+            b1 = b0;
+            b0 = B(x, k);
+        } else if (b1 <= c) {    // too low (x < hi, since b1 is the sentinel at hi)
+            ++x;
+            b0 = b1;
+            b1 = x < hi ? B(x + 1, k) : ~0ull;
+        } else {
+            v = x;
+            cv = b0;
+            return b0 <= c || x == lo;
+        }
+    }
+    return false;
+}
+
+// The same decoding by a whole (converged) warp: each vertex with k = i+1 <=
+// 4 from binom_root, otherwise (or if its correction runs out) by a 32-ary
+// search (lane L tests lo + L * step; the tested values C(x, k) grow with
+// x, so the passing lanes form a prefix), two dependent table reads per
+// vertex for n <= 1024.  Every lane computes and receives the same v.
 template <int Q>
 __device__ __forceinline__ void warp_decode_simplex(const Binom& B, uint64_t c, int64_t top, int* v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = Q; i >= 0; --i) {
         int64_t lo = i, hi = top;  // C(lo, i+1) <= c holds throughout
-        while (lo < hi) {
-            const int64_t step = (hi - lo + 32) >> 5;  // ceil((hi - lo + 1) / 32)
-            const int64_t x = lo + (int64_t)lane * step;
-            const bool ok = x <= hi && B(x, i + 1) <= c;
-            const int L = 31 - __clz((int)__ballot_sync(0xffffffffu, ok));
-            lo += (int64_t)L * step;
-            hi = min(hi, lo + step - 1);
+        int64_t r;
+        uint64_t cr;
+        if (i + 1 <= 4 && binom_root(B, c, i + 1, lo, hi, r, cr)) {
+            v[i] = (int)r;
+            c -= cr;
+            top = r - 1;
+            continue;
+        } else {
+            while (lo < hi) {
+                const int64_t step = (hi - lo + 32) >> 5;  // ceil((hi - lo + 1) / 32)
+                const int64_t x = lo + (int64_t)lane * step;
+                const bool ok = x <= hi && B(x, i + 1) <= c;
+                const int L = 31 - __clz((int)__ballot_sync(0xffffffffu, ok));
+                lo += (int64_t)L * step;
+                hi = min(hi, lo + step - 1);
+            }
         }
         v[i] = (int)lo;
         c -= B(lo, i + 1);
