@@ -25,8 +25,9 @@
 // (the argument behind Lemma 5.2.10).  Columns finalized in one round have
 // strictly decreasing keys, hence distinct pivots.
 //
-// Phase 1: one warp per column, at most 8 additions, all columns at once;
-// finished columns that needed additions keep their reduced form.  Phase 2:
+// Phase 1: one warp per column, at most 8 additions (none when there are
+// at most four columns per SM), all columns at once; finished columns that
+// needed additions keep their reduced form.  Phase 2:
 // one block per remaining column (the front/back engine of
 // reduce_device.cuh), state kept across rounds, at most 128 additions per
 // round so that finalized pivots reach waiting columns early; a column
@@ -302,8 +303,18 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         const int64_t cap = 8192;
         uint64_t* scratch = ws.alloc_n<uint64_t>((size_t)slots * 2 * cap);
         VR_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s));
-        k_reduce_round<P><<<(unsigned)(slots / RED_WARPS), RED_WARPS * 32, 0, s>>>(c, U, u, 8, cur_key, status, adds,
-                                                                                   scratch, cap, ctr);
+        // Phase 1 is a throughput engine for many short columns; with at most
+        // four columns per SM the block engine takes every column at once, and
+        // warp-engine additions of a column that does not finish here would be
+        // redone, so phase 1 then only settles the columns needing no addition.
+        int sms = 148;
+        {
+            int dev = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        const int p1_budget = u <= 4 * (int64_t)sms ? 0 : 8;
+        k_reduce_round<P><<<(unsigned)(slots / RED_WARPS), RED_WARPS * 32, 0, s>>>(c, U, u, p1_budget, cur_key, status,
+                                                                                   adds, scratch, cap, ctr);
         k_finalize<<<1, 1024, 0, s>>>(c, e, U, u, cur_key, status, adds, Un, ctr + 1, ctr + 2);
         VR_CUDA(cudaGetLastError());
         VR_CUDA(cudaMemcpyAsync(&hs.p[8], ctr + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
