@@ -80,10 +80,15 @@ k_reduce_round(Ctx c, const uint32_t* __restrict__ U, int64_t u, int budget, uin
 }
 
 
-__global__ void __launch_bounds__(1024)
-k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint64_t* __restrict__ cur_key,
-           const uint8_t* __restrict__ status, const uint32_t* __restrict__ adds, uint32_t* __restrict__ Unext,
-           unsigned long long* __restrict__ u_next, unsigned long long* __restrict__ first_status) {
+// Finalize a round with one block (any multiple of 32 threads): in order,
+// column j is final iff complete and its key is below the prefix minimum of
+// the earlier unfinished keys; the rest go, in order, to Unext.  The round's
+// keys, states and addition counts were written by other blocks of the same
+// kernel (heavy rounds) or by an earlier kernel, so they are read through L2.
+__device__ void finalize_rows(const Ctx& c, const Emit& e, const uint32_t* __restrict__ U, int64_t u,
+                              const uint64_t* cur_key, const uint8_t* status, const uint32_t* adds,
+                              uint32_t* __restrict__ Unext, unsigned long long* __restrict__ u_next,
+                              unsigned long long* __restrict__ first_status) {
     __shared__ uint64_t wmin[32];
     __shared__ uint32_t wcnt[32];
     __shared__ uint64_t carry_min;
@@ -96,8 +101,8 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
         const int64_t k = base + threadIdx.x;
         const bool valid = k < u;
         const uint32_t j = valid ? U[k] : 0;
-        const uint64_t key = valid ? cur_key[j] : EMPTY;
-        const uint8_t st = valid ? status[j] : ST_COMPLETE;
+        const uint64_t key = valid ? __ldcg(cur_key + j) : EMPTY;
+        const uint8_t st = valid ? __ldcg(status + j) : ST_COMPLETE;
         // inclusive min-scan within the warp
         uint64_t incl = key;
 #pragma unroll
@@ -126,7 +131,7 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
         if (excl < pm) pm = excl;
         const bool fin = valid && st == ST_COMPLETE && (key == EMPTY || key < pm);
         if (k == 0) *first_status = st;
-        if (fin) finish_column(c, e, j, key, adds[j]);
+        if (fin) finish_column(c, e, j, key, __ldcg(adds + j));
         const bool keep = valid && !fin;
         const uint32_t kb = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) wcnt[wid] = __popc(kb);
@@ -150,16 +155,21 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
     if (threadIdx.x == 0) *u_next = carry_cnt;
 }
 
+__global__ void __launch_bounds__(1024)
+k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint64_t* __restrict__ cur_key,
+           const uint8_t* __restrict__ status, const uint32_t* __restrict__ adds, uint32_t* __restrict__ Unext,
+           unsigned long long* __restrict__ u_next, unsigned long long* __restrict__ first_status) {
+    finalize_rows(c, e, U, u, cur_key, status, adds, Unext, u_next, first_status);
+}
+
 
 template <int P>
-__global__ void __launch_bounds__(HT, 1)
-k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t* __restrict__ slot_of,
-               HeavyState hs, int budget, int keybits, uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status,
-               uint32_t* __restrict__ adds_out) {
+__device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64_t k,
+                             const uint32_t* __restrict__ slot_of, const HeavyState& hs, int budget, int keybits,
+                             uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status,
+                             uint32_t* __restrict__ adds_out) {
     extern __shared__ __align__(16) unsigned char hsm[];
     HeavySmem& S = *reinterpret_cast<HeavySmem*>(hsm);
-    const int64_t k = blockIdx.x;
-    if (k >= u) return;
     const int64_t j = U[k];
     const int64_t slot = slot_of[j];
     uint64_t* B = hs.B + slot * hs.bcap;
@@ -268,6 +278,32 @@ k_reduce_heavy(Ctx c, const uint32_t* __restrict__ U, int64_t u, const uint32_t*
     }
 }
 
+// One round of the block engine: block k reduces column U[k] for k < *d_u
+// (the count the previous round left on the device; the grid may be larger),
+// and the last block to finish finalizes the round into Unext / *d_unext.
+// No block waits for another, so rounds can be queued without the host.
+template <int P>
+__global__ void __launch_bounds__(HT, 1)
+k_reduce_heavy(Ctx c, Emit e, const uint32_t* __restrict__ U, const unsigned long long* __restrict__ d_u,
+               const uint32_t* __restrict__ slot_of, HeavyState hs, int budget, int keybits,
+               uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status, uint32_t* __restrict__ adds_out,
+               uint32_t* __restrict__ Unext, unsigned long long* __restrict__ d_unext,
+               unsigned long long* __restrict__ first_status, unsigned int* __restrict__ done) {
+    __shared__ int last;
+    const int64_t u = (int64_t)*d_u;
+    if ((int64_t)blockIdx.x < u) heavy_column<P>(c, U, blockIdx.x, slot_of, hs, budget, keybits, cur_key, status, adds_out);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    finalize_rows(c, e, U, u, cur_key, status, adds_out, Unext, d_unext, first_status);
+    if (threadIdx.x == 0) *done = 0;  // ready for the next round (launched after this kernel ends)
+}
+
 __global__ void k_assign_slots(const uint32_t* __restrict__ U, int64_t u, uint32_t* __restrict__ slot_of,
                                uint8_t* __restrict__ init) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x) {
@@ -353,35 +389,53 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         int64_t stalled_adds = 0;  // additions granted to the first column since a column was last finalized
         cudaEvent_t ev[2] = {nullptr, nullptr};
         if (h.prof) { VR_CUDA(cudaEventCreate(&ev[0])); VR_CUDA(cudaEventCreate(&ev[1])); }
+        // Each round leaves its unfinished count on the device (du[0] / du[1]
+        // alternate with U / Un), so rounds are queued `chunk` at a time and
+        // the host only looks between chunks; a round queued after the last
+        // column finished has nothing to do.  VR_LOG=1 looks after every round.
+        unsigned long long* du = ws.zeros_n<unsigned long long>(3);  // counts [0] [1], first status [2]
+        unsigned int* done = ws.zeros_n<unsigned int>(1);
+        VR_CUDA(cudaMemcpyAsync(du, ctr + 1, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+        int cur = 0;
+        const int chunk = log_enabled() ? 1 : 8;
         while (u > 0) {
-            if (h.prof) {
-                VR_CUDA(cudaMemsetAsync(h.prof + 6, 0, 2 * sizeof(unsigned long long), s));
-                VR_CUDA(cudaEventRecord(ev[0], s));
+            const int64_t u0 = u;
+            int granted = 0;
+            for (int r = 0; r < chunk; ++r) {
+                if (h.prof) {
+                    VR_CUDA(cudaMemsetAsync(h.prof + 6, 0, 2 * sizeof(unsigned long long), s));
+                    VR_CUDA(cudaEventRecord(ev[0], s));
+                }
+                k_reduce_heavy<P><<<(unsigned)u0, HT, smem, s>>>(c, e, U, du + cur, slot_of, h, budget, keybits,
+                                                                   cur_key, status, adds, Un, du + (cur ^ 1), du + 2,
+                                                                   done);
+                VR_CUDA(cudaGetLastError());
+                if (h.prof) VR_CUDA(cudaEventRecord(ev[1], s));
+                uint32_t* t = U; U = Un; Un = t;
+                cur ^= 1;
+                ++rounds;
+                granted += budget;
+                if (budget < budget_cap) budget *= 2;
             }
-            k_reduce_heavy<P><<<(unsigned)u, HT, smem, s>>>(c, U, u, slot_of, h, budget, keybits, cur_key, status, adds);
-            if (h.prof) VR_CUDA(cudaEventRecord(ev[1], s));
-            k_finalize<<<1, 1024, 0, s>>>(c, e, U, u, cur_key, status, adds, Un, ctr + 1, ctr + 2);
-            VR_CUDA(cudaGetLastError());
-            VR_CUDA(cudaMemcpyAsync(&hs.p[8], ctr + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaMemcpyAsync(&hs.p[8], du + cur, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaMemcpyAsync(&hs.p[9], du + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             if (h.prof)
                 VR_CUDA(cudaMemcpyAsync(&hs.p[24], h.prof + 6, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             VR_CUDA(cudaStreamSynchronize(s));
             const int64_t un = hs.p[8];
             const int64_t first = hs.p[9];
-            ++rounds;
             if (log_enabled()) {
                 float ms = 0.f;
                 if (h.prof) VR_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
                 fprintf(stderr,
                         "[vr] dim%d block round %d: budget %d bcap %lld: %lld -> %lld unfinished; %.3f ms, "
                         "max additions %lld, max block cycles %lld\n",
-                        P, rounds, budget, (long long)h.bcap, (long long)u, (long long)un, ms, (long long)hs.p[24],
+                        P, rounds, budget, (long long)h.bcap, (long long)u0, (long long)un, ms, (long long)hs.p[24],
                         (long long)hs.p[25]);
             }
-            uint32_t* t = U; U = Un; Un = t;
-            const bool stalled = un == u;
+            const bool stalled = un == u0;
             u = un;
-            stalled_adds = stalled ? stalled_adds + budget : 0;
+            stalled_adds = stalled ? stalled_adds + granted : 0;
             if (stalled_adds > ((int64_t)1 << 24)) throw Error{VR_ERR_INTERNAL};  // no column can need this many
             if (stalled && first == ST_OVERFLOW) {
                 // the first column outgrew its back buffer: give the remaining
@@ -395,7 +449,6 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
                 VR_CUDA(cudaGetLastError());
             }
-            if (budget < budget_cap) budget *= 2;
         }
         if (h.prof) {
             VR_CUDA(cudaEventDestroy(ev[0]));
