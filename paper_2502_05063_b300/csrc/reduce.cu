@@ -29,7 +29,7 @@
 // at most four columns per SM), all columns at once; finished columns that
 // needed additions keep their reduced form.  Phase 2:
 // one block per remaining column (the front/back engine of
-// reduce_device.cuh), state kept across rounds, at most 128 additions per
+// reduce_device.cuh), state kept across rounds, at most 64 additions per
 // round so that finalized pivots reach waiting columns early; a column
 // whose pivot belongs to a column finished in phase 2 adds that column's
 // reduced form.  The first unfinished column can never be blocked, so every
@@ -384,8 +384,8 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         int budget = 64;
         // Columns are finalized between rounds only, so a round that runs as
         // long as its longest column would keep columns it unblocks idle; a
-        // cap of 128 additions (about 1 ms) keeps rounds short.
-        constexpr int budget_cap = 128;
+        // cap of 64 additions (about 0.5 ms) keeps rounds short.
+        constexpr int budget_cap = 64;
         int64_t stalled_adds = 0;  // additions granted to the first column since a column was last finalized
         cudaEvent_t ev[2] = {nullptr, nullptr};
         if (h.prof) { VR_CUDA(cudaEventCreate(&ev[0])); VR_CUDA(cudaEventCreate(&ev[1])); }
