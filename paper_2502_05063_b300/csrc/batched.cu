@@ -548,11 +548,13 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             bool ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, s);
             uint64_t key = EMPTY;
             unsigned long long col_adds = 0;
+            int pre = 0;  // owner kind of the current pivot if probed during the last merge (3: none)
             while (ok) {
                 if (++col_adds > (1ull << 22)) { ok = false; break; }  // far beyond any column: flag the cloud
                 if (S.fsize == 0 && !heavy_refill(S, back, 32 + TRI_BITS)) { key = EMPTY; break; }
                 key = S.buf[S.cur][0];
-                const int kind = heavy_owner_probe<1>(c, S, key, self_key);
+                const int kind = pre ? (pre == 3 ? 0 : pre) : heavy_owner_probe<1>(c, S, key, self_key);
+                pre = 0;
                 if (kind == 0) break;
                 if (kind == 1) {
                     const int64_t opos = S.opos;
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
                         ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, o);
                     }
                 } else {
-                    const int r = heavy_apparent_add<1>(c, S, back, BACKCAP);
+                    const int r = heavy_apparent_add<1>(c, S, back, BACKCAP, self_key, &pre);
                     if (r < 0) break;  // the pivot has no owner: the column is complete
                     ok = r > 0;
                 }

@@ -195,6 +195,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
     uint64_t key = ok ? EMPTY : 0;  // 0: no consistent state yet, the smallest (always valid) bound
     uint8_t st = ST_COMPLETE;
     int done = 0;
+    int pre = 0;  // owner kind of the current pivot if probed during the last merge (3: none)
     long long t0 = clock64(), t_ref = 0, t_look = 0, t_add = 0, n_look = 0;
     const long long t_resume = t0;
     while (ok) {
@@ -203,7 +204,10 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
         long long tb = clock64();
         t_ref += tb - ta;
         key = S.buf[S.cur][0];
-        const int kind = heavy_owner_probe<P>(c, S, key, self_key);
+        // the owner of this pivot may have been probed during the last merge
+        const int kind = pre ? (pre == 3 ? 0 : pre) : heavy_owner_probe<P>(c, S, key, self_key);
+        if (pre && threadIdx.x == 0 && key != S.sel) atomicExch(c.err, DEV_INTERNAL);
+        pre = 0;
         long long tc = clock64();
         t_look += tc - tb;
         ++n_look;
@@ -229,7 +233,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
                 ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, o);
             }
         } else {
-            const int r = heavy_apparent_add<P>(c, S, B, hs.bcap);
+            const int r = heavy_apparent_add<P>(c, S, B, hs.bcap, self_key, &pre);
             if (r < 0) {  // s' is not apparent: the pivot has no owner, the column is complete
                 if (hs.prof && threadIdx.x == 0) S.tp[15] += clock64();
                 break;
@@ -252,13 +256,13 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
         atomicMax(hs.prof + 6, (unsigned long long)done);
         atomicMax(hs.prof + 7, (unsigned long long)(clock64() - t_resume));
         const long long tot = clock64() - t_resume;
-        if (tot > 1500000 && done >= 100)
+        if (tot > 500000 && done >= 60)
             printf("[vr] dim%d col %lld: %d adds %lld cycles: refill %lld lookup %lld add %lld | gen %lld sort %lld "
                    "merge %lld multiset %lld (%lld) | refill sample %lld count %lld compact %lld sort %lld (%lld) "
                    "back %lld front %d\n",
                    P, (long long)j, done, tot, t_ref, t_look, t_add, S.tp[0], S.tp[1], S.tp[2], S.tp[3], S.tp[8],
                    S.tp[4], S.tp[5], S.tp[6], S.tp[7], S.tp[9], (long long)S.bsize, S.fsize);
-        if (tot > 1500000 && done >= 100)
+        if (tot > 500000 && done >= 60)
             printf("[vr] dim%d col %lld: merge search+scan %lld place %lld swap+spill %lld | owner hash/decode %lld "
                    "apparent scan %lld | add total %lld | t0 search %lld, merges %lld, mean a %lld b %lld\n",
                    P, (long long)j, S.tp[10], S.tp[11], S.tp[12], S.tp[13], S.tp[14], S.tp[15], S.tp[16], S.tp[19],

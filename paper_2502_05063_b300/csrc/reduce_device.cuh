@@ -482,9 +482,11 @@ struct HeavySmem {
     int fsize;
     int cur;               // which buf holds the front
     int flag;
+    int na;                // merge result size (written by the merge group)
+    int pkind;             // owner kind of the next pivot, probed during the merge (0: not probed)
     int ov[VR_MAX_DIM + 2];
     uint32_t orank;
-    uint64_t sel;          // radix-select result
+    uint64_t sel;          // the next pivot, when found during a merge
     long long tp[20];      // VR_LOG only (thread 0): sub-phase cycles
 };
 #define HPROF_T0() long long _hp_t = clock64()
@@ -582,7 +584,17 @@ __device__ bool heavy_append(HeavySmem& S, uint64_t* B, int64_t bcap, const uint
     return true;
 }
 
-// front <- front XOR stage[0..b), stage sorted, unique and entirely below Ks.
+// Named barrier `id` over `n` threads (whole warps); id 0 with n = HT is
+// the block barrier.
+__device__ __forceinline__ void bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// F2 <- F XOR run (F = buf[cur] with a rows, run = stage[0..b), both sorted
+// and unique), computed by threads [t0, t0 + nt) of the block, which meet at
+// barrier `bar`; returns the merged size.  No barrier follows the writes of
+// F2 (the caller's does).
+//
 // Merge path: the merged sequence (a + b rows before cancellation) is cut
 // into equal diagonals, one per thread, so rows that cluster in one gap of
 // the front still spread over the threads.  Each thread finds the split of
@@ -593,16 +605,14 @@ __device__ bool heavy_append(HeavySmem& S, uint64_t* B, int64_t bcap, const uint
 // run rows are marked in a bit mask, so a thread's output offset is its
 // diagonal minus twice the cancelled run rows before its range, without a
 // block scan.
-__device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
-    if (b == 0) return true;
+__device__ int merge_group(HeavySmem& S, int cur, int a, int b, int t0, int nt, int bar) {
     const uint64_t* run = S.stage;
-    const uint64_t* F = S.buf[S.cur];
-    uint64_t* F2 = S.buf[S.cur ^ 1];
-    const int a = S.fsize;
-    HPROF_T0();
+    const uint64_t* F = S.buf[cur];
+    uint64_t* F2 = S.buf[cur ^ 1];
+    const int g = (int)threadIdx.x - t0;
     const int tot = a + b;
-    const int per = (tot + HT - 1) / HT;
-    const int d = min(tot, (int)threadIdx.x * per);
+    const int per = (tot + nt - 1) / nt;
+    const int d = min(tot, g * per);
     int lo = max(0, d - a), hi = min(d, b);
     while (lo < hi) {
         const int m = (lo + hi) >> 1;
@@ -611,10 +621,10 @@ __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b
     const int k0 = lo;
     int i0 = d - lo;
     if (i0 > 0 && k0 < b && F[i0 - 1] == run[k0]) --i0;
-    S.msplit[threadIdx.x] = ((uint32_t)i0 << 16) | (uint32_t)k0;
-    if (threadIdx.x < HSTAGE / 32) S.eqbits[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t nx = threadIdx.x + 1 < HT ? S.msplit[threadIdx.x + 1] : (((uint32_t)a << 16) | (uint32_t)b);
+    S.msplit[g] = ((uint32_t)i0 << 16) | (uint32_t)k0;
+    if (g < HSTAGE / 32) S.eqbits[g] = 0;
+    bar_sync(bar, nt);
+    const uint32_t nx = g + 1 < nt ? S.msplit[g + 1] : (((uint32_t)a << 16) | (uint32_t)b);
     const int i1 = (int)(nx >> 16), k1 = (int)(nx & 0xFFFFu);
     {
         int i = i0, k = k0;
@@ -625,20 +635,13 @@ __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b
             k += y <= x;
         }
     }
-    if (threadIdx.x == 0) { S.tp[16] += clock64() - _hp_t; S.tp[17] += a; S.tp[18] += b; S.tp[19] += 1; }
-    __syncthreads();
+    bar_sync(bar, nt);
     int eb = 0, et = 0;
     for (int w = 0; w < ((b + 31) >> 5); ++w) {
         const uint32_t m = S.eqbits[w];
         const int base = w << 5;
         et += __popc(m);
         eb += base + 32 <= k0 ? __popc(m) : (base < k0 ? __popc(m & ((1u << (k0 - base)) - 1u)) : 0);
-    }
-    const int na = tot - 2 * et;
-    HPROF_LAP(10);
-    if (threadIdx.x == 0) {  // every read of cur and fsize happened before the last barrier
-        S.cur ^= 1;
-        S.fsize = min(na, FKEEP);
     }
     {
         int pos = i0 + k0 - 2 * eb;
@@ -652,15 +655,37 @@ __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b
         while (i < i1) F2[pos++] = F[i++];
         while (k < k1) F2[pos++] = run[k++];
     }
+    return tot - 2 * et;
+}
+
+// After a merge into buf[cur ^ 1] of na rows (cur and fsize already
+// published): spill the top of the front to B and lower the split.
+__device__ bool heavy_spill(HeavySmem& S, uint64_t* B, int64_t bcap, int na) {
+    if (na <= FKEEP) return true;
+    uint64_t* F2 = S.buf[S.cur];
+    if (!heavy_append(S, B, bcap, F2 + FKEEP, na - FKEEP)) return false;
+    if (threadIdx.x == 0) S.Ks = F2[FKEEP];
+    __syncthreads();
+    return true;
+}
+
+// front <- front XOR stage[0..b), stage sorted, unique and entirely below Ks
+// (the whole block merges; see merge_group).
+__device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
+    if (b == 0) return true;
+    const int cur = S.cur, a = S.fsize;
+    HPROF_T0();
+    const int na = merge_group(S, cur, a, b, 0, HT, 0);
+    HPROF_LAP(10);
+    if (threadIdx.x == 0) {  // every read of cur and fsize happened before the merge's first barrier
+        S.cur = cur ^ 1;
+        S.fsize = min(na, FKEEP);
+    }
     __syncthreads();
     HPROF_LAP(11);
-    if (na > FKEEP) {  // spill the top of the front to B and lower the split
-        if (!heavy_append(S, B, bcap, F2 + FKEEP, na - FKEEP)) return false;
-        if (threadIdx.x == 0) S.Ks = F2[FKEEP];
-        __syncthreads();
-    }
+    const bool ok = heavy_spill(S, B, bcap, na);
     HPROF_LAP(12);
-    return true;
+    return ok;
 }
 
 // W <- W + run for a sorted, unique run in stage[0..b) (any keys).
@@ -900,6 +925,91 @@ __device__ bool heavy_cob_place(HeavySmem& S, uint64_t* B, int64_t bcap, bool ok
     return true;
 }
 
+template <int P, bool GROUP = false>
+__device__ int heavy_owner_probe(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t self_key);
+
+// True if x is in the sorted array a[0..len).
+__device__ __forceinline__ bool sorted_has(const uint64_t* a, int len, uint64_t x) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (a[m] < x) lo = m + 1; else hi = m;
+    }
+    return lo < len && a[lo] == x;
+}
+
+// heavy_cob_place for the last (here: only) pass of an addition, with the
+// owner probe of the next pivot overlapped with the merge.  The next pivot
+// is the smallest row of F XOR run; warp 0 finds it from the first 32 rows
+// of each (a head row survives iff it is not in the other array; the result
+// is certain when it precedes row 32 of both), then warps 0 and 1 probe its
+// owner while warps 2..15 merge.  S.pkind receives the probe's kind, or 0
+// when the pivot was not certain from the heads (or the column emptied);
+// every thread returns it in *next_kind (3 = probed, no owner).
+template <int P>
+__device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, bool ok, uint64_t key,
+                                     uint64_t self_key, int* next_kind) {
+    const int64_t bs = S.bsize;
+    const bool lt = ok && key < S.Ks;
+    const bool ge = ok && !lt;
+    int tot;
+    const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
+    const int nlt = tot & 0xFFFF, nge = tot >> 16;
+    if (bs + nge > bcap) return false;
+    if (ge) B[bs + (packed >> 16)] = key;
+    if (lt) S.stage[packed & 0xFFFF] = key;
+    if (threadIdx.x == 0) {
+        S.bsize = bs + nge;
+        S.pkind = 0;
+        atomicAdd(&g_heavy_counts[1], (unsigned long long)nlt);
+        atomicAdd(&g_heavy_counts[2], (unsigned long long)nge);
+        atomicAdd(&g_heavy_counts[3], 1ull);
+    }
+    __syncthreads();
+    stage_sort(S, nlt);
+    *next_kind = 0;
+    if (nlt == 0) return true;
+    const int cur = S.cur, a = S.fsize;  // read by every thread before the groups part
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wid >= 2) {
+        const int na = merge_group(S, cur, a, nlt, 64, HT - 64, 1);
+        if (threadIdx.x == 64) {
+            S.na = na;
+            S.cur = cur ^ 1;
+            S.fsize = min(na, FKEEP);
+        }
+    } else {
+        const uint64_t* F = S.buf[cur];
+        const uint64_t* run = S.stage;
+        uint64_t pn = EMPTY;
+        bool certain = false;
+        if (wid == 0) {
+            const uint64_t f = lane < a ? F[lane] : EMPTY, r = lane < nlt ? run[lane] : EMPTY;
+            const uint64_t cf = (f != EMPTY && !sorted_has(run, nlt, f)) ? f : EMPTY;
+            const uint64_t cr = (r != EMPTY && !sorted_has(F, a, r)) ? r : EMPTY;
+            pn = cf < cr ? cf : cr;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint64_t y = __shfl_xor_sync(0xffffffffu, pn, o);
+                pn = y < pn ? y : pn;
+            }
+            const uint64_t f32 = a > 32 ? F[32] : EMPTY, r32 = nlt > 32 ? run[32] : EMPTY;
+            certain = pn < (f32 < r32 ? f32 : r32);
+            if (lane == 0) { S.sel = certain ? pn : EMPTY; }
+        }
+        bar_sync(2, 64);
+        pn = S.sel;
+        if (pn != EMPTY) {
+            const int kind = heavy_owner_probe<P, true>(c, S, pn, self_key);
+            if (threadIdx.x == 0) S.pkind = kind == 0 ? 3 : kind;  // 3: the pivot has no owner
+        }
+    }
+    __syncthreads();
+    const int na = S.na;
+    *next_kind = S.pkind;
+    return heavy_spill(S, B, bcap, na);
+}
+
 // Row key of x + {w} for the thread's w, if w is no vertex of x and the
 // cofacet is within the threshold.
 template <int P>
@@ -1045,7 +1155,10 @@ __device__ bool heavy_add_multiset(HeavySmem& S, uint64_t* B, int64_t bcap, cons
 // the dropped vertex in S.ov[P+1], the diameter rank in S.orank), 0 = none.
 // A row has at most one owner: warp 1 probes the hash of finished columns
 // while warp 0 decodes the pivot and finds the dropped vertex.
-template <int P>
+// With GROUP the probe is made by warps 0 and 1 alone (named barrier 2),
+// while the rest of the block merges; the result is then read by those two
+// warps only, until the block meets again.
+template <int P, bool GROUP>
 __device__ int heavy_owner_probe(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t self_key) {
     constexpr int NT = P + 2;
     constexpr int NPAIR = NT * (NT - 1) / 2;
@@ -1088,7 +1201,7 @@ __device__ int heavy_owner_probe(const Ctx& c, HeavySmem& S, uint64_t rk, uint64
             }
         }
     }
-    __syncthreads();
+    if (GROUP) bar_sync(2, 64); else __syncthreads();
     HPROF_LAP(13);
     return S.opos >= 0 ? 1 : S.flag;
 }
@@ -1117,12 +1230,16 @@ __device__ bool heavy_apparent_check(const Ctx& c, HeavySmem& S) {
 }
 
 // For a probe that returned 2: if s' owns the pivot, W <- W + D_{s'} and 1;
-// -1 if it does not (the pivot has no owner); 0 if B overflowed.  When one
+// -1 if it does not (the pivot has no owner); 0 if B overflowed.
+// *next_kind: the owner kind of the next pivot when it was probed during
+// the merge (see heavy_cob_place_next), else 0.  When one
 // pass of HT vertices covers every w above the dropped vertex, the ownership
 // test and the first pass of D_{s'} share their rank reads: each thread's
 // w is an older cofacet of s' exactly when its diameter stays at s''s.
 template <int P>
-__device__ int heavy_apparent_add(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap) {
+__device__ int heavy_apparent_add(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, uint64_t self_key,
+                                  int* next_kind) {
+    *next_kind = 0;
     const int64_t n = c.R.n;
     Simplex<P> o;
 #pragma unroll
@@ -1150,6 +1267,8 @@ __device__ int heavy_apparent_add(const Ctx& c, HeavySmem& S, uint64_t* B, int64
     }
     if (__syncthreads_or(older)) return -1;
     HPROF_LAP(14);
+    if (n <= HT)  // this was the only pass: probe the next pivot's owner during the merge
+        return heavy_cob_place_next<P>(c, S, B, bcap, ok, key, self_key, next_kind) ? 1 : 0;
     if (!heavy_cob_place(S, B, bcap, ok, key)) return 0;
     return heavy_add_coboundary<P>(c, S, B, bcap, o, n - 1 - HT) ? 1 : 0;
 }
