@@ -263,8 +263,8 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
                    P, (long long)j, done, tot, t_ref, t_look, t_add, S.tp[0], S.tp[1], S.tp[2], S.tp[3], S.tp[8],
                    S.tp[4], S.tp[5], S.tp[6], S.tp[7], S.tp[9], (long long)S.bsize, S.fsize);
         if (tot > 500000 && done >= 60)
-            printf("[vr] dim%d col %lld: merge search+scan %lld place %lld swap+spill %lld | owner hash/decode %lld "
-                   "apparent scan %lld | add total %lld | t0 search %lld, merges %lld, mean a %lld b %lld\n",
+            printf("[vr] dim%d col %lld: head check %lld, wait for merge %lld, spill %lld | owner probe %lld "
+                   "apparent test+gen %lld | add total %lld | merge group %lld, merges %lld, mean a %lld b %lld\n",
                    P, (long long)j, S.tp[10], S.tp[11], S.tp[12], S.tp[13], S.tp[14], S.tp[15], S.tp[16], S.tp[19],
                    S.tp[17] / (S.tp[19] ? S.tp[19] : 1), S.tp[18] / (S.tp[19] ? S.tp[19] : 1));
     }

@@ -941,14 +941,16 @@ __device__ __forceinline__ bool sorted_has(const uint64_t* a, int len, uint64_t 
 // heavy_cob_place for the last (here: only) pass of an addition, with the
 // owner probe of the next pivot overlapped with the merge.  The next pivot
 // is the smallest row of F XOR run; warp 0 finds it from the first 32 rows
-// of each (a head row survives iff it is not in the other array; the result
-// is certain when it precedes row 32 of both), then warps 0 and 1 probe its
-// owner while warps 2..15 merge.  S.pkind receives the probe's kind, or 0
+// of each (merged by a bitonic network in registers, where a row survives
+// unless an equal row sits next to it; the result is certain when it
+// precedes row 32 of both), then warps 0 and 1 probe its owner while warps
+// 2..15 merge.  S.pkind receives the probe's kind, or 0
 // when the pivot was not certain from the heads (or the column emptied);
 // every thread returns it in *next_kind (3 = probed, no owner).
 template <int P>
 __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, bool ok, uint64_t key,
                                      uint64_t self_key, int* next_kind) {
+    HPROF_T0();
     const int64_t bs = S.bsize;
     const bool lt = ok && key < S.Ks;
     const bool ge = ok && !lt;
@@ -966,14 +968,21 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
         atomicAdd(&g_heavy_counts[3], 1ull);
     }
     __syncthreads();
+    HPROF_LAP(0);
     stage_sort(S, nlt);
+    HPROF_LAP(1);
     *next_kind = 0;
     if (nlt == 0) return true;
     const int cur = S.cur, a = S.fsize;  // read by every thread before the groups part
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (wid >= 2) {
+        const long long tm = clock64();
         const int na = merge_group(S, cur, a, nlt, 64, HT - 64, 1);
         if (threadIdx.x == 64) {
+            S.tp[16] += clock64() - tm;  // merge group alone
+            S.tp[17] += a;
+            S.tp[18] += nlt;
+            S.tp[19] += 1;
             S.na = na;
             S.cur = cur ^ 1;
             S.fsize = min(na, FKEEP);
@@ -984,20 +993,39 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
         uint64_t pn = EMPTY;
         bool certain = false;
         if (wid == 0) {
-            const uint64_t f = lane < a ? F[lane] : EMPTY, r = lane < nlt ? run[lane] : EMPTY;
-            const uint64_t cf = (f != EMPTY && !sorted_has(run, nlt, f)) ? f : EMPTY;
-            const uint64_t cr = (r != EMPTY && !sorted_has(F, a, r)) ? r : EMPTY;
-            pn = cf < cr ? cf : cr;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const uint64_t y = __shfl_xor_sync(0xffffffffu, pn, o);
-                pn = y < pn ? y : pn;
+            // bitonic merge of the two 32-row heads in registers: lane L holds
+            // positions L (front head) and 32 + L (run head, reversed)
+            uint64_t e0 = lane < a ? F[lane] : EMPTY, e1 = (31 - lane) < nlt ? run[31 - lane] : EMPTY;
+            {
+                const uint64_t lo = e0 < e1 ? e0 : e1, hi = e0 < e1 ? e1 : e0;
+                e0 = lo;
+                e1 = hi;
             }
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) {
+                const uint64_t o0 = __shfl_xor_sync(0xffffffffu, e0, j), o1 = __shfl_xor_sync(0xffffffffu, e1, j);
+                const bool low = (lane & j) == 0;
+                e0 = low ? (e0 < o0 ? e0 : o0) : (e0 < o0 ? o0 : e0);
+                e1 = low ? (e1 < o1 ? e1 : o1) : (e1 < o1 ? o1 : e1);
+            }
+            // equal rows are adjacent pairs (each array is unique); a row survives
+            // unless a neighbour equals it
+            const uint64_t p0 = __shfl_up_sync(0xffffffffu, e0, 1), n0 = __shfl_down_sync(0xffffffffu, e0, 1);
+            const uint64_t p1 = __shfl_up_sync(0xffffffffu, e1, 1), n1 = __shfl_down_sync(0xffffffffu, e1, 1);
+            const uint64_t last0 = __shfl_sync(0xffffffffu, e0, 31), first1 = __shfl_sync(0xffffffffu, e1, 0);
+            const uint64_t prev0 = lane == 0 ? EMPTY - 1 : p0, next0 = lane == 31 ? first1 : n0;
+            const uint64_t prev1 = lane == 0 ? last0 : p1, next1 = lane == 31 ? EMPTY - 1 : n1;
+            const bool s0 = e0 != EMPTY && e0 != prev0 && e0 != next0;
+            const bool s1 = e1 != EMPTY && e1 != prev1 && e1 != next1;
+            const uint32_t b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
+            pn = b0 ? __shfl_sync(0xffffffffu, e0, __ffs(b0) - 1)
+                    : (b1 ? __shfl_sync(0xffffffffu, e1, __ffs(b1) - 1) : EMPTY);
             const uint64_t f32 = a > 32 ? F[32] : EMPTY, r32 = nlt > 32 ? run[32] : EMPTY;
             certain = pn < (f32 < r32 ? f32 : r32);
             if (lane == 0) { S.sel = certain ? pn : EMPTY; }
         }
         bar_sync(2, 64);
+        HPROF_LAP(10);  // head check
         pn = S.sel;
         if (pn != EMPTY) {
             const int kind = heavy_owner_probe<P, true>(c, S, pn, self_key);
@@ -1005,9 +1033,12 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
         }
     }
     __syncthreads();
+    HPROF_LAP(11);  // wait for the merge group
     const int na = S.na;
     *next_kind = S.pkind;
-    return heavy_spill(S, B, bcap, na);
+    const bool r = heavy_spill(S, B, bcap, na);
+    HPROF_LAP(12);
+    return r;
 }
 
 // Row key of x + {w} for the thread's w, if w is no vertex of x and the
