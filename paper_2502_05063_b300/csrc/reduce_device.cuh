@@ -534,18 +534,19 @@ __device__ void block_bitonic(uint64_t* a, int len) {
         }
 }
 
-// Sort stage[0..cnt) ascending.  Up to HT rows: each thread ranks its row by
-// comparing it with every row (broadcast shared reads, stable for equal
-// rows) and places it, which costs one barrier instead of the log^2 barrier
-// stages of a bitonic network; more rows use the bitonic network.
-__device__ void stage_sort(HeavySmem& S, int cnt) {
-    if (cnt <= 1) return;
+// Sort stage[0..cnt) ascending; returns where the sorted rows are.  Up to
+// HT rows: each thread ranks its row by comparing it with every row
+// (broadcast shared reads, stable for equal rows) and places it in the
+// upper half of the stage, which costs one barrier instead of the log^2
+// barrier stages of a bitonic network; more rows are sorted in place by the
+// bitonic network.
+__device__ const uint64_t* stage_sort(HeavySmem& S, int cnt) {
+    if (cnt <= 1) return S.stage;
     if (cnt <= HT && cnt <= HSTAGE / 2) {
         const int i = threadIdx.x;
-        uint64_t x = 0;
-        int rank = 0;
         if (i < cnt) {
-            x = S.stage[i];
+            const uint64_t x = S.stage[i];
+            int rank = 0;
             for (int j = 0; j < cnt; ++j) {
                 const uint64_t y = S.stage[j];
                 rank += (y < x) || (y == x && j < i);
@@ -553,15 +554,14 @@ __device__ void stage_sort(HeavySmem& S, int cnt) {
             S.stage[HSTAGE / 2 + rank] = x;
         }
         __syncthreads();
-        if (i < cnt) S.stage[i] = S.stage[HSTAGE / 2 + i];
-        __syncthreads();
-        return;
+        return S.stage + HSTAGE / 2;
     }
     int len = 2;
     while (len < cnt) len <<= 1;
     for (int i = cnt + threadIdx.x; i < len; i += HT) S.stage[i] = EMPTY;
     __syncthreads();
     block_bitonic(S.stage, len);
+    return S.stage;
 }
 
 __device__ __forceinline__ int lower_bound_sm(const uint64_t* a, int len, uint64_t x) {
@@ -590,7 +590,7 @@ __device__ __forceinline__ void bar_sync(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// F2 <- F XOR run (F = buf[cur] with a rows, run = stage[0..b), both sorted
+// F2 <- F XOR run (F = buf[cur] with a rows, run[0..b) in the stage, both sorted
 // and unique), computed by threads [t0, t0 + nt) of the block, which meet at
 // barrier `bar`; returns the merged size.  No barrier follows the writes of
 // F2 (the caller's does).
@@ -605,8 +605,7 @@ __device__ __forceinline__ void bar_sync(int id, int n) {
 // run rows are marked in a bit mask, so a thread's output offset is its
 // diagonal minus twice the cancelled run rows before its range, without a
 // block scan.
-__device__ int merge_group(HeavySmem& S, int cur, int a, int b, int t0, int nt, int bar) {
-    const uint64_t* run = S.stage;
+__device__ int merge_group(HeavySmem& S, const uint64_t* run, int cur, int a, int b, int t0, int nt, int bar) {
     const uint64_t* F = S.buf[cur];
     uint64_t* F2 = S.buf[cur ^ 1];
     const int g = (int)threadIdx.x - t0;
@@ -669,13 +668,13 @@ __device__ bool heavy_spill(HeavySmem& S, uint64_t* B, int64_t bcap, int na) {
     return true;
 }
 
-// front <- front XOR stage[0..b), stage sorted, unique and entirely below Ks
-// (the whole block merges; see merge_group).
-__device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
+// front <- front XOR run[0..b) (rows in the stage, sorted, unique and
+// entirely below Ks; the whole block merges, see merge_group).
+__device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, const uint64_t* run, int b) {
     if (b == 0) return true;
     const int cur = S.cur, a = S.fsize;
     HPROF_T0();
-    const int na = merge_group(S, cur, a, b, 0, HT, 0);
+    const int na = merge_group(S, run, cur, a, b, 0, HT, 0);
     HPROF_LAP(10);
     if (threadIdx.x == 0) {  // every read of cur and fsize happened before the merge's first barrier
         S.cur = cur ^ 1;
@@ -692,7 +691,7 @@ __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, int b
 __device__ bool heavy_add_run(HeavySmem& S, uint64_t* B, int64_t bcap, int b) {
     const int lo = lower_bound_sm(S.stage, b, S.Ks);
     if (!heavy_append(S, B, bcap, S.stage + lo, b - lo)) return false;
-    return heavy_merge_front(S, B, bcap, lo);
+    return heavy_merge_front(S, B, bcap, S.stage, lo);
 }
 
 // Remove the holes (EMPTY) from B in place, keeping the order of the rest.
@@ -918,9 +917,9 @@ __device__ bool heavy_cob_place(HeavySmem& S, uint64_t* B, int64_t bcap, bool ok
     }
     __syncthreads();
     HPROF_LAP(0);
-    stage_sort(S, nlt);
+    const uint64_t* srt = stage_sort(S, nlt);
     HPROF_LAP(1);
-    if (!heavy_merge_front(S, B, bcap, nlt)) return false;
+    if (!heavy_merge_front(S, B, bcap, srt, nlt)) return false;
     HPROF_LAP(2);
     return true;
 }
@@ -969,7 +968,7 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
     }
     __syncthreads();
     HPROF_LAP(0);
-    stage_sort(S, nlt);
+    const uint64_t* srt = stage_sort(S, nlt);
     HPROF_LAP(1);
     *next_kind = 0;
     if (nlt == 0) return true;
@@ -977,7 +976,7 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (wid >= 2) {
         const long long tm = clock64();
-        const int na = merge_group(S, cur, a, nlt, 64, HT - 64, 1);
+        const int na = merge_group(S, srt, cur, a, nlt, 64, HT - 64, 1);
         if (threadIdx.x == 64) {
             S.tp[16] += clock64() - tm;  // merge group alone
             S.tp[17] += a;
@@ -989,7 +988,7 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
         }
     } else {
         const uint64_t* F = S.buf[cur];
-        const uint64_t* run = S.stage;
+        const uint64_t* run = srt;
         uint64_t pn = EMPTY;
         bool certain = false;
         if (wid == 0) {
@@ -1090,21 +1089,21 @@ __device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_
 // Sort stage[0..cnt) (cnt <= HSTAGE), keep one row of every run of odd
 // length (Z/2) and add the result to W.
 __device__ bool heavy_flush_stage(HeavySmem& S, uint64_t* B, int64_t bcap, int cnt) {
-    stage_sort(S, cnt);
+    const uint64_t* srt = stage_sort(S, cnt);
     bool keep0 = false, keep1 = false;
     const int i0 = threadIdx.x, i1 = threadIdx.x + HT;
     uint64_t v0 = 0, v1 = 0;
-    if (i0 < cnt && (i0 == 0 || S.stage[i0 - 1] != S.stage[i0])) {
+    if (i0 < cnt && (i0 == 0 || srt[i0 - 1] != srt[i0])) {
         int e = i0;
-        while (e + 1 < cnt && S.stage[e + 1] == S.stage[i0]) ++e;
+        while (e + 1 < cnt && srt[e + 1] == srt[i0]) ++e;
         keep0 = ((e - i0 + 1) & 1) != 0;
-        v0 = S.stage[i0];
+        v0 = srt[i0];
     }
-    if (i1 < cnt && (S.stage[i1 - 1] != S.stage[i1])) {
+    if (i1 < cnt && (srt[i1 - 1] != srt[i1])) {
         int e = i1;
-        while (e + 1 < cnt && S.stage[e + 1] == S.stage[i1]) ++e;
+        while (e + 1 < cnt && srt[e + 1] == srt[i1]) ++e;
         keep1 = ((e - i1 + 1) & 1) != 0;
-        v1 = S.stage[i1];
+        v1 = srt[i1];
     }
     // rows 0..HT-1 first, then HT..2HT-1, so the kept rows stay in order
     int tot0, tot1;
