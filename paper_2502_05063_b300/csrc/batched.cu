@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             const uint64_t self_key = cols[j];
             Simplex<1> s;
             load_col<1>(c, self_key, s);
-            if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.Ks = EMPTY; S.cur = 0; }
+            if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.holes = 0; S.Ks = EMPTY; S.cur = 0; }
             __syncthreads();
             bool ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, s);
             uint64_t key = EMPTY;

@@ -181,12 +181,14 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
     uint32_t adds;
     bool ok = true;
     if (!hs.init[slot]) {
-        if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.Ks = EMPTY; S.cur = 0; }
+        if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.holes = 0; S.Ks = EMPTY; S.cur = 0; }
         __syncthreads();
         adds = 0;
         ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, s);
     } else {
-        if (threadIdx.x == 0) { S.fsize = hs.fsize[slot]; S.bsize = hs.bsize[slot]; S.Ks = hs.Ks[slot]; S.cur = 0; }
+        if (threadIdx.x == 0) {
+            S.fsize = hs.fsize[slot]; S.bsize = hs.bsize[slot]; S.holes = hs.holes[slot]; S.Ks = hs.Ks[slot]; S.cur = 0;
+        }
         adds = hs.adds[slot];
         __syncthreads();
         for (int i = threadIdx.x; i < S.fsize; i += HT) S.buf[0][i] = hs.F[slot * FC + i];
@@ -273,6 +275,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
     if (threadIdx.x == 0) {
         hs.fsize[slot] = S.fsize;
         hs.bsize[slot] = S.bsize;
+        hs.holes[slot] = S.holes;
         hs.Ks[slot] = S.Ks;
         hs.adds[slot] = adds;
         hs.init[slot] = ok ? 1 : 0;  // an overflowed column restarts from scratch
@@ -381,6 +384,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         h.bsize = ws.alloc_n<int64_t>(nslot);
         h.init = ws.alloc_n<uint8_t>(nslot);
         h.adds = ws.alloc_n<uint32_t>(nslot);
+        h.holes = ws.alloc_n<int64_t>(nslot);
         h.prof = log_enabled() ? ws.zeros_n<unsigned long long>(8) : nullptr;
         uint32_t* slot_of = ws.alloc_n<uint32_t>(m);
         VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));  // no slot: phase-1 columns

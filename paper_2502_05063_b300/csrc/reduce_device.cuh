@@ -463,6 +463,7 @@ struct HeavyState {
     int64_t* bsize;
     uint8_t* init;     // 0: the column has not been started (or must restart)
     uint32_t* adds;
+    int64_t* holes;    // per slot: holes (EMPTY rows) in B
     unsigned long long* prof;  // VR_LOG only: cycles {refill, lookup, add, resume}, counts {adds, lookups}
 };
 
@@ -478,6 +479,7 @@ struct HeavySmem {
     uint32_t hist[256];
     uint64_t Ks;
     int64_t bsize;
+    int64_t holes;         // EMPTY rows in B (left by refills)
     int64_t opos;
     int fsize;
     int cur;               // which buf holds the front
@@ -748,9 +750,7 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
     static_assert(NS <= FC, "the sample lives in the front buffer");
     __shared__ int cnt_sh;
     __shared__ unsigned long long min_sh;
-    __shared__ unsigned long long holes_sh;
     const int lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     for (;;) {
         __syncthreads();
         const int64_t bsz = S.bsize;
@@ -772,59 +772,65 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
             T = Sm[q];
         }
         HPROF_LAP(4);
+        // 2. positions of the rows below T (one pass; the smallest row is only
+        //    looked for when T has to be lowered to it)
         int cnt;
-        uint64_t bmin;
-        int64_t holes;
+        uint64_t bmin = EMPTY;
+        bool have_min = false;
         for (;;) {
-            if (threadIdx.x == 0) { cnt_sh = 0; min_sh = EMPTY; holes_sh = 0; }
+            if (threadIdx.x == 0) cnt_sh = 0;
             __syncthreads();
-            uint64_t mn = EMPTY;
-            int hl = 0;
-            // warp-uniform trip count: every lane reaches the ballots
-            for (int64_t w0 = (int64_t)threadIdx.x - lane; w0 < bsz; w0 += (int64_t)HT * UN) {
+            // UN rows per thread per step; a mask of the rows below T, and the
+            // rare hits placed by one shared-memory atomic per lane
+            for (int64_t w0 = threadIdx.x; w0 < bsz; w0 += (int64_t)HT * UN) {
                 uint64_t kk[UN];
 #pragma unroll
                 for (int u = 0; u < UN; ++u) {
-                    const int64_t i = w0 + (int64_t)u * HT + lane;
+                    const int64_t i = w0 + (int64_t)u * HT;
                     kk[u] = i < bsz ? B[i] : EMPTY;
-                    hl += i < bsz && kk[u] == EMPTY;
                 }
+                uint32_t mask = 0;
 #pragma unroll
-                for (int u = 0; u < UN; ++u) {
-                    const bool lt = kk[u] < T;
-                    mn = kk[u] < mn ? kk[u] : mn;
-                    const uint32_t m = __ballot_sync(0xffffffffu, lt);
-                    if (m) {
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(&cnt_sh, __popc(m));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        const int slot = base + __popc(m & lt_mask);
-                        if (lt && slot < FC) G[slot] = (uint64_t)(w0 + (int64_t)u * HT + lane);
-                    }
+                for (int u = 0; u < UN; ++u) mask |= (uint32_t)(kk[u] < T) << u;
+                if (mask) {
+                    int slot = atomicAdd(&cnt_sh, __popc(mask));
+#pragma unroll
+                    for (int u = 0; u < UN; ++u)
+                        if ((mask >> u) & 1u) {
+                            if (slot < FC) G[slot] = (uint64_t)(w0 + (int64_t)u * HT);
+                            ++slot;
+                        }
                 }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const uint64_t y = __shfl_xor_sync(0xffffffffu, mn, o);
-                mn = y < mn ? y : mn;
-                hl += __shfl_xor_sync(0xffffffffu, hl, o);
-            }
-            if (lane == 0) {
-                atomicMin(&min_sh, (unsigned long long)mn);
-                atomicAdd(&holes_sh, (unsigned long long)hl);
             }
             __syncthreads();
             cnt = cnt_sh;
-            bmin = min_sh;
-            holes = (int64_t)holes_sh;
             __syncthreads();
-            if (bmin == EMPTY) {  // only holes left: the column is zero
-                if (threadIdx.x == 0) S.bsize = 0;
-                __syncthreads();
-                return false;
-            }
             if (cnt >= 1 && cnt <= FC) break;
-            if (cnt > FC && T == bmin + 1) break;  // one key with more copies than fit
+            if (cnt > FC && have_min && T == bmin + 1) break;  // one key with more copies than fit
+            if (!have_min) {
+                if (threadIdx.x == 0) min_sh = EMPTY;
+                __syncthreads();
+                uint64_t mn = EMPTY;
+                for (int64_t i = threadIdx.x; i < bsz; i += HT) {
+                    const uint64_t k = B[i];
+                    mn = k < mn ? k : mn;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, mn, o);
+                    mn = y < mn ? y : mn;
+                }
+                if (lane == 0) atomicMin(&min_sh, (unsigned long long)mn);
+                __syncthreads();
+                bmin = min_sh;
+                have_min = true;
+                __syncthreads();
+                if (bmin == EMPTY) {  // only holes left: the column is zero
+                    if (threadIdx.x == 0) S.bsize = 0;
+                    __syncthreads();
+                    return false;
+                }
+            }
             if (cnt == 0 || q <= 1) {
                 T = bmin + 1;  // the smallest key alone
             } else {
@@ -843,7 +849,6 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
                 S.Ks = T;
             }
             __syncthreads();
-            holes += cnt;
         } else {
             // gather the rows and leave holes
             for (int i = threadIdx.x; i < cnt; i += HT) {
@@ -851,7 +856,6 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
                 G[i] = B[pos];
                 B[pos] = EMPTY;
             }
-            holes += cnt;
             int len = 1;
             while (len < cnt) len <<= 1;
             for (int i = cnt + threadIdx.x; i < len; i += HT) G[i] = EMPTY;
@@ -884,11 +888,17 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
             }
             __syncthreads();
         }
+        const int64_t holes = S.holes + cnt;
         if (holes == bsz) {
-            if (threadIdx.x == 0) S.bsize = 0;
+            if (threadIdx.x == 0) { S.bsize = 0; S.holes = 0; }
             __syncthreads();
         } else if (2 * holes > bsz) {
             heavy_compact_back(S, B);
+            if (threadIdx.x == 0) S.holes = 0;
+            __syncthreads();
+        } else {
+            if (threadIdx.x == 0) S.holes = holes;
+            __syncthreads();
         }
         HPROF_LAP(7);
         if (S.fsize > 0) return true;
