@@ -181,7 +181,7 @@ __device__ void emit_block(const BatchArgs& A, BatchSmem& M, int p, int cloud, c
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
+__global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char bsm[];
     BatchSmem& M = *reinterpret_cast<BatchSmem*>(bsm);
     HeavySmem& S = M.S;
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
             int pre = 0;  // owner kind of the current pivot if probed during the last merge (3: none)
             while (ok) {
                 if (++col_adds > (1ull << 22)) { ok = false; break; }  // far beyond any column: flag the cloud
-                if (S.fsize == 0 && !heavy_refill(S, back, 32 + TRI_BITS)) { key = EMPTY; break; }
+                if (S.fsize == 0 && !heavy_refill<8>(S, back)) { key = EMPTY; break; }
                 key = S.buf[S.cur][0];
                 const int kind = pre ? (pre == 3 ? 0 : pre) : heavy_owner_probe<1>(c, S, key, self_key);
                 pre = 0;
@@ -566,7 +566,8 @@ __global__ void __launch_bounds__(HT) k_batched(BatchArgs A) {
                         ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, o);
                     }
                 } else {
-                    const int r = heavy_apparent_add<1>(c, S, back, BACKCAP, self_key, &pre);
+                    // small clouds: the plain merge (the overlapped probe does not pay here)
+                    const int r = heavy_apparent_add<1, false>(c, S, back, BACKCAP, self_key, &pre);
                     if (r < 0) break;  // the pivot has no owner: the column is complete
                     ok = r > 0;
                 }

@@ -165,7 +165,7 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
 
 template <int P>
 __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64_t k,
-                             const uint32_t* __restrict__ slot_of, const HeavyState& hs, int budget, int keybits,
+                             const uint32_t* __restrict__ slot_of, const HeavyState& hs, int budget,
                              uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status,
                              uint32_t* __restrict__ adds_out) {
     extern __shared__ __align__(16) unsigned char hsm[];
@@ -202,7 +202,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
     const long long t_resume = t0;
     while (ok) {
         long long ta = clock64();
-        if (S.fsize == 0 && !heavy_refill(S, B, keybits)) { key = EMPTY; break; }  // zero column
+        if (S.fsize == 0 && !heavy_refill(S, B)) { key = EMPTY; break; }  // zero column
         long long tb = clock64();
         t_ref += tb - ta;
         key = S.buf[S.cur][0];
@@ -292,13 +292,13 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
 template <int P>
 __global__ void __launch_bounds__(HT, 1)
 k_reduce_heavy(Ctx c, Emit e, const uint32_t* __restrict__ U, const unsigned long long* __restrict__ d_u,
-               const uint32_t* __restrict__ slot_of, HeavyState hs, int budget, int keybits,
+               const uint32_t* __restrict__ slot_of, HeavyState hs, int budget,
                uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status, uint32_t* __restrict__ adds_out,
                uint32_t* __restrict__ Unext, unsigned long long* __restrict__ d_unext,
                unsigned long long* __restrict__ first_status, unsigned int* __restrict__ done) {
     __shared__ int last;
     const int64_t u = (int64_t)*d_u;
-    if ((int64_t)blockIdx.x < u) heavy_column<P>(c, U, blockIdx.x, slot_of, hs, budget, keybits, cur_key, status, adds_out);
+    if ((int64_t)blockIdx.x < u) heavy_column<P>(c, U, blockIdx.x, slot_of, hs, budget, cur_key, status, adds_out);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -337,7 +337,6 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
     k_iota<<<(unsigned)((m + 255) / 256 < 4096 ? (m + 255) / 256 : 4096), 256, 0, s>>>(U, m);
     VR_CUDA(cudaGetLastError());
     int64_t u = m;
-    const int keybits = bits_for(c.rmask) + c.rcb;
     // Phase 1: one warp per column, at most 8 additions, every column at once.
     {
         const int64_t max_slots = 148 * 4 * RED_WARPS;
@@ -414,7 +413,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                     VR_CUDA(cudaMemsetAsync(h.prof + 6, 0, 2 * sizeof(unsigned long long), s));
                     VR_CUDA(cudaEventRecord(ev[0], s));
                 }
-                k_reduce_heavy<P><<<(unsigned)u0, HT, smem, s>>>(c, e, U, du + cur, slot_of, h, budget, keybits,
+                k_reduce_heavy<P><<<(unsigned)u0, HT, smem, s>>>(c, e, U, du + cur, slot_of, h, budget,
                                                                    cur_key, status, adds, Un, du + (cur ^ 1), du + 2,
                                                                    done);
                 VR_CUDA(cudaGetLastError());

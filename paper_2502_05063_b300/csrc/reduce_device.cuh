@@ -743,10 +743,10 @@ __device__ void heavy_compact_back(HeavySmem& S, uint64_t* B) {
 // those rows are gathered, replaced by holes (EMPTY, above every row key),
 // sorted, and the rows of odd multiplicity become the front (Z/2).  B is
 // only read in full; it is compacted once holes make up half of it.
-__device__ bool heavy_refill(HeavySmem& S, uint64_t* B, int keybits) {
-    (void)keybits;
+// UN: rows each thread loads per step of the pass (independent loads in flight).
+template <int UN = 16>
+__device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
     constexpr int NS = 2048;  // samples (fit the empty front buffer)
-    constexpr int UN = 8;     // independent loads in flight per thread
     static_assert(NS <= FC, "the sample lives in the front buffer");
     __shared__ int cnt_sh;
     __shared__ unsigned long long min_sh;
@@ -1276,7 +1276,7 @@ __device__ bool heavy_apparent_check(const Ctx& c, HeavySmem& S) {
 // pass of HT vertices covers every w above the dropped vertex, the ownership
 // test and the first pass of D_{s'} share their rank reads: each thread's
 // w is an older cofacet of s' exactly when its diameter stays at s''s.
-template <int P>
+template <int P, bool OVERLAP = true>
 __device__ int heavy_apparent_add(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, uint64_t self_key,
                                   int* next_kind) {
     *next_kind = 0;
@@ -1307,7 +1307,7 @@ __device__ int heavy_apparent_add(const Ctx& c, HeavySmem& S, uint64_t* B, int64
     }
     if (__syncthreads_or(older)) return -1;
     HPROF_LAP(14);
-    if (n <= HT)  // this was the only pass: probe the next pivot's owner during the merge
+    if (OVERLAP && n <= HT)  // this was the only pass: probe the next pivot's owner during the merge
         return heavy_cob_place_next<P>(c, S, B, bcap, ok, key, self_key, next_kind) ? 1 : 0;
     if (!heavy_cob_place(S, B, bcap, ok, key)) return 0;
     return heavy_add_coboundary<P>(c, S, B, bcap, o, n - 1 - HT) ? 1 : 0;
