@@ -113,7 +113,8 @@ static void check_dev_err(const int* dev_err, cudaStream_t s) {
     int h = 0;
     VR_CUDA(cudaMemcpyAsync(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     VR_CUDA(cudaStreamSynchronize(s));
-    switch (h) {
+    if (h != DEV_OK && log_enabled()) fprintf(stderr, "[vr] device error %d (site %d)\n", h & 0xFF, h >> 8);
+    switch (h & 0xFF) {  // the upper bits name the failing check (DEV_INTERNAL)
         case DEV_OK: return;
         case DEV_CAPACITY: throw Error{VR_ERR_OOM};
         case DEV_TIMEOUT: throw Error{VR_ERR_TIMEOUT};

@@ -33,9 +33,9 @@
 // round so that finalized pivots reach waiting columns early; a column
 // whose pivot belongs to a column finished in phase 2 adds that column's
 // reduced form.  The first unfinished column can never be blocked, so every
-// round makes progress (it is finalized or gains its additions); a stall
-// with an overflowing first column moves the remaining columns to larger
-// buffers (VR_ERR_OOM if they cannot grow).
+// round makes progress (it is finalized or gains its additions); if the
+// first column overflows its back buffer in a batch of rounds, the remaining
+// columns restart with at least twice the room (VR_ERR_OOM past 2^31 rows).
 //
 // Pivot lookup (the paper's two-layer store, Fig 5.10): first a device hash
 // of pivots found by this reduction, then the apparent pairs, which are not
@@ -82,7 +82,9 @@ k_reduce_round(Ctx c, const uint32_t* __restrict__ U, int64_t u, int budget, uin
 
 // Finalize a round with one block (any multiple of 32 threads): in order,
 // column j is final iff complete and its key is below the prefix minimum of
-// the earlier unfinished keys; the rest go, in order, to Unext.  The round's
+// the earlier unfinished keys; the rest go, in order, to Unext.  If the first
+// column overflowed, *first_status becomes ST_OVERFLOW (and stays so until
+// the host clears it: rounds are checked in batches).  The round's
 // keys, states and addition counts were written by other blocks of the same
 // kernel (heavy rounds) or by an earlier kernel, so they are read through L2.
 __device__ void finalize_rows(const Ctx& c, const Emit& e, const uint32_t* __restrict__ U, int64_t u,
@@ -130,7 +132,7 @@ __device__ void finalize_rows(const Ctx& c, const Emit& e, const uint32_t* __res
         if (wmin[wid] < pm) pm = wmin[wid];
         if (excl < pm) pm = excl;
         const bool fin = valid && st == ST_COMPLETE && (key == EMPTY || key < pm);
-        if (k == 0) *first_status = st;
+        if (k == 0 && st == ST_OVERFLOW) *first_status = ST_OVERFLOW;  // sticky until the host clears it
         if (fin) finish_column(c, e, j, key, __ldcg(adds + j));
         const bool keep = valid && !fin;
         const uint32_t kb = __ballot_sync(0xffffffffu, keep);
@@ -208,7 +210,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
         key = S.buf[S.cur][0];
         // the owner of this pivot may have been probed during the last merge
         const int kind = pre ? (pre == 3 ? 0 : pre) : heavy_owner_probe<P>(c, S, key, self_key);
-        if (pre && threadIdx.x == 0 && key != S.sel) atomicExch(c.err, DEV_INTERNAL);
+        if (pre && threadIdx.x == 0 && key != S.sel) atomicExch(c.err, DEV_INTERNAL | (1 << 8));
         pre = 0;
         long long tc = clock64();
         t_look += tc - tb;
@@ -324,6 +326,14 @@ __global__ void k_iota(uint32_t* U, int64_t m) {
         U[k] = (uint32_t)k;
 }
 
+// Rows of the arena the block engine's back buffers share.
+int64_t heavy_arena_rows() {
+    const char* v = getenv("VR_HEAVY_ARENA_LOG2");
+    int lg = v ? atoi(v) : 28;
+    lg = lg < 16 ? 16 : (lg > 30 ? 30 : lg);
+    return (int64_t)1 << lg;
+}
+
 template <int P>
 void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
     const int64_t m = c.num_cols;
@@ -375,7 +385,9 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         VR_CUDA(cudaFuncSetAttribute(k_reduce_heavy<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int64_t nslot = u;
         HeavyState h;
-        h.bcap = std::max<int64_t>((int64_t)1 << 16, std::min<int64_t>((int64_t)1 << 22, ((int64_t)1 << 27) / nslot));
+        // back buffers share an arena of 2^28 rows (2 GB; VR_HEAVY_ARENA_LOG2 overrides, for tests)
+        const int64_t arena = heavy_arena_rows();
+        h.bcap = std::max<int64_t>((int64_t)1 << 16, std::min<int64_t>((int64_t)1 << 22, arena / nslot));
         h.F = ws.alloc_n<uint64_t>((size_t)nslot * FC);
         h.B = ws.alloc_n<uint64_t>((size_t)nslot * h.bcap);
         h.Ks = ws.alloc_n<uint64_t>(nslot);
@@ -408,6 +420,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         while (u > 0) {
             const int64_t u0 = u;
             int granted = 0;
+            VR_CUDA(cudaMemsetAsync(du + 2, 0, sizeof(unsigned long long), s));
             for (int r = 0; r < chunk; ++r) {
                 if (h.prof) {
                     VR_CUDA(cudaMemsetAsync(h.prof + 6, 0, 2 * sizeof(unsigned long long), s));
@@ -444,12 +457,14 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
             u = un;
             stalled_adds = stalled ? stalled_adds + granted : 0;
             if (stalled_adds > ((int64_t)1 << 24)) throw Error{VR_ERR_INTERNAL};  // no column can need this many
-            if (stalled && first == ST_OVERFLOW) {
-                // the first column outgrew its back buffer: give the remaining
-                // columns the whole arena (they restart from scratch)
-                const int64_t nb = ((int64_t)1 << 27) / (u > 0 ? u : 1);
-                if (nb <= h.bcap) throw Error{VR_ERR_OOM};
-                h.bcap = std::min<int64_t>(nb, (int64_t)1 << 27);
+            if (first == ST_OVERFLOW && u > 0) {
+                // the first column (which no other column can block) outgrew its
+                // back buffer in this batch: the remaining columns restart from
+                // scratch with at least twice the room (the whole arena when
+                // that is more), up to 2^31 rows in all
+                const int64_t nb = std::max<int64_t>(2 * h.bcap, arena / u) & ~(int64_t)15;
+                if ((double)nb * (double)u > (double)((int64_t)1 << 31)) throw Error{VR_ERR_OOM};
+                h.bcap = nb;
                 h.B = ws.alloc_n<uint64_t>((size_t)u * h.bcap);
                 // slots are reassigned: finished columns lose their stored forms
                 VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));

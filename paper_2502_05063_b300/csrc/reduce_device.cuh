@@ -260,7 +260,7 @@ __device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex
         const int64_t pos = warp_hash_find(c, ct);
         if (pos >= 0) {
             const uint64_t okey = c.cols[pos];
-            if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL);
+            if (!(okey < self_key)) atomicExch(c.err, DEV_INTERNAL | (2 << 8));
             load_col<P>(c, okey, o);
             opos = pos;
             return true;
@@ -303,7 +303,7 @@ __device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex
 #pragma unroll
     for (int q = 0; q <= P; ++q) cs += c.B(o.v[q], q + 1);
     o.cidx = cs;
-    if (!(col_key<P>(c, o) < self_key)) atomicExch(c.err, DEV_INTERNAL);
+    if (!(col_key<P>(c, o) < self_key)) atomicExch(c.err, DEV_INTERNAL | (3 << 8));
     opos = -1;
     return true;
 }
@@ -1211,7 +1211,7 @@ __device__ int heavy_owner_probe(const Ctx& c, HeavySmem& S, uint64_t rk, uint64
         const int64_t hp = warp_hash_find(c, ct);
         if (lane == 0) {
             S.opos = hp;
-            if (hp >= 0 && !(c.cols[hp] < self_key)) atomicExch(c.err, DEV_INTERNAL);  // owners come earlier
+            if (hp >= 0 && !(c.cols[hp] < self_key)) atomicExch(c.err, DEV_INTERNAL | (4 << 8));  // owners come earlier
         }
     }
     if (wid == 0) {

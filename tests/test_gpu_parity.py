@@ -8,6 +8,8 @@ import json
 import math
 import os
 import struct
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -250,3 +252,28 @@ def test_workload_golden(vr, name):
             assert bc.stats[p]["apparent"] == g["apparent"][p]
             assert bc.stats[p]["pairs"] == g["pairs"][p]
             assert bc.stats[p]["essential"] == g["essential"][p]
+
+
+def test_back_buffer_regrowth_matches_golden(vr):
+    """Columns whose back buffers overflow restart with more room; the pairing is unchanged.
+
+    With a 2^21-row arena for the block engine's back buffers (64K rows per
+    column) the long cocycle columns of torus500 (several 100K rows) overflow
+    again and again; each overflow of the first unfinished column, in any
+    round of a batch, must enlarge the buffers.  Runs in a child process,
+    which reads the arena size from its environment.
+    """
+    here = os.path.dirname(os.path.abspath(__file__))
+    script = (
+        "import sys\n"
+        "sys.path[:0] = [%r, %r]\n"
+        "from test_gpu_parity import load_golden, rows_gpu\n"
+        "from paper_2502_05063_b300 import vr\n"
+        "g, pts, thr, dg = load_golden('torus500')\n"
+        "bc = vr.barcodes(points=pts, dmax=g['dmax'], threshold=thr)\n"
+        "bad = [p for p in range(g['dmax'] + 1) if rows_gpu(bc, p) != dg[p]]\n"
+        "print('MISMATCH' if bad else 'OK', bad)\n" % (os.path.dirname(here), here))
+    env = dict(os.environ, VR_HEAVY_ARENA_LOG2="21")
+    out = subprocess.run([sys.executable, "-c", script], env=env, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-3000:]
+    assert out.stdout.strip().startswith("OK"), out.stdout
