@@ -593,9 +593,9 @@ __device__ __forceinline__ void bar_sync(int id, int n) {
 }
 
 // F2 <- F XOR run (F = buf[cur] with a rows, run[0..b) in the stage, both sorted
-// and unique), computed by threads [t0, t0 + nt) of the block, which meet at
-// barrier `bar`; returns the merged size.  No barrier follows the writes of
-// F2 (the caller's does).
+// and unique), computed by threads [t0, t0 + nt) of the block (t0 and nt
+// multiples of 32), which meet at barrier `bar`; returns the merged size.
+// No barrier follows the writes of F2 (the caller's does).
 //
 // Merge path: the merged sequence (a + b rows before cancellation) is cut
 // into equal diagonals, one per thread, so rows that cluster in one gap of
@@ -603,14 +603,16 @@ __device__ __forceinline__ void bar_sync(int id, int n) {
 // its diagonal by a binary search no longer than log2(b) (equal rows ordered
 // front first; a boundary between a front row and an equal run row moves
 // before the front row, so every cancelling pair stays in one thread's
-// range) and reads the end of its range from the next thread.  Cancelled
-// run rows are marked in a bit mask, so a thread's output offset is its
-// diagonal minus twice the cancelled run rows before its range, without a
-// block scan.
+// range) and reads the end of its range from the next thread.  Meanwhile
+// each run row looks itself up in the front: the cancelled ones form a bit
+// mask (one ballot per 32 rows), so after one barrier a thread's output
+// offset is its diagonal minus twice the cancelled run rows before its
+// range, and a single walk writes its part.
 __device__ int merge_group(HeavySmem& S, const uint64_t* run, int cur, int a, int b, int t0, int nt, int bar) {
     const uint64_t* F = S.buf[cur];
     uint64_t* F2 = S.buf[cur ^ 1];
     const int g = (int)threadIdx.x - t0;
+    const int lane = threadIdx.x & 31;
     const int tot = a + b;
     const int per = (tot + nt - 1) / nt;
     const int d = min(tot, g * per);
@@ -623,20 +625,21 @@ __device__ int merge_group(HeavySmem& S, const uint64_t* run, int cur, int a, in
     int i0 = d - lo;
     if (i0 > 0 && k0 < b && F[i0 - 1] == run[k0]) --i0;
     S.msplit[g] = ((uint32_t)i0 << 16) | (uint32_t)k0;
-    if (g < HSTAGE / 32) S.eqbits[g] = 0;
+    // run rows kb + lane (kb: this warp's block of 32, stepping by nt) that cancel
+    for (int kb = g - lane; kb < b; kb += nt) {
+        const int k = kb + lane;
+        bool eq = false;
+        if (k < b) {
+            const uint64_t y = run[k];
+            const int q = lower_bound_sm(F, a, y);
+            eq = q < a && F[q] == y;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, eq);
+        if (lane == 0) S.eqbits[kb >> 5] = m;
+    }
     bar_sync(bar, nt);
     const uint32_t nx = g + 1 < nt ? S.msplit[g + 1] : (((uint32_t)a << 16) | (uint32_t)b);
     const int i1 = (int)(nx >> 16), k1 = (int)(nx & 0xFFFFu);
-    {
-        int i = i0, k = k0;
-        while (i < i1 && k < k1) {
-            const uint64_t x = F[i], y = run[k];
-            if (x == y) atomicOr(&S.eqbits[k >> 5], 1u << (k & 31));
-            i += x <= y;
-            k += y <= x;
-        }
-    }
-    bar_sync(bar, nt);
     int eb = 0, et = 0;
     for (int w = 0; w < ((b + 31) >> 5); ++w) {
         const uint32_t m = S.eqbits[w];
@@ -644,17 +647,15 @@ __device__ int merge_group(HeavySmem& S, const uint64_t* run, int cur, int a, in
         et += __popc(m);
         eb += base + 32 <= k0 ? __popc(m) : (base < k0 ? __popc(m & ((1u << (k0 - base)) - 1u)) : 0);
     }
-    {
-        int pos = i0 + k0 - 2 * eb;
-        int i = i0, k = k0;
-        while (i < i1 && k < k1) {
-            const uint64_t x = F[i], y = run[k];
-            if (x < y) { F2[pos++] = x; ++i; }
-            else if (y < x) { F2[pos++] = y; ++k; }
-            else { ++i; ++k; }
-        }
-        while (i < i1) F2[pos++] = F[i++];
-        while (k < k1) F2[pos++] = run[k++];
+    int pos = i0 + k0 - 2 * eb;
+    int i = i0, k = k0;
+    while (i < i1 || k < k1) {
+        const uint64_t x = i < i1 ? F[i] : EMPTY;
+        const uint64_t y = k < k1 ? run[k] : EMPTY;
+        const bool tx = x <= y, ty = y <= x;  // both: a cancelling pair
+        if (tx != ty) F2[pos++] = tx ? x : y;
+        i += tx;
+        k += ty;
     }
     return tot - 2 * et;
 }
