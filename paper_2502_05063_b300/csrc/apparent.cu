@@ -57,12 +57,17 @@ k_filtration_apparent(RankMatrix R, Binom B, uint32_t thr, const uint32_t* __res
     constexpr int K_LANE = 32;                 // vertices each lane tests for its own column first
     for (uint64_t chunk = warp; chunk * 32 < num_cand; chunk += nwarps) {
         const uint64_t c = chunk * 32 + lane;
+        // the warp decodes its first index once; lane L's index is L more, which
+        // in the combinatorial number system (eq. 5.6) adds L to the smallest
+        // vertex unless that reaches the next one (then the lane decodes itself)
         int v[NV];
+        warp_decode_simplex<P>(B, chunk * 32, n - 1, v);
+        v[0] += lane;
         uint32_t pr[NPS > 0 ? NPS : 1];  // ranks of the pairs of s, pair k = (a, b), a > b, in pair_of order
         uint32_t r = 0;
         bool kept = false;
         if (c < num_cand) {
-            decode_simplex<P>(B, c, n - 1, v);
+            if (v[0] >= v[1]) decode_simplex<P>(B, c, n - 1, v);
             int k = 0;
 #pragma unroll
             for (int a = 1; a < NV; ++a)
@@ -92,9 +97,9 @@ k_filtration_apparent(RankMatrix R, Binom B, uint32_t thr, const uint32_t* __res
 #pragma unroll
                 for (int a = 0; a < NV; ++a) ok = ok && (w != v[a]);
                 if (ok) {
-                    uint32_t rr[NV];
+                    uint32_t rr[NV];  // row w of the symmetric matrix: lanes with consecutive v[0] read one line
 #pragma unroll
-                    for (int a = 0; a < NV; ++a) rr[a] = R(v[a], w);
+                    for (int a = 0; a < NV; ++a) rr[a] = R(w, v[a]);
 #pragma unroll
                     for (int a = 0; a < NV; ++a) ok = ok && (rr[a] <= r);
                     if (ok) {

@@ -196,8 +196,9 @@ struct RankMatrix {
     const uint32_t* r;
     int64_t n;
     int64_t ld;
+    // indices are below 2^31, so one 32x32->64 multiply-add forms the offset
     __device__ __forceinline__ uint32_t operator()(int64_t i, int64_t j) const {
-        return __ldg(r + (size_t)i * (size_t)ld + (size_t)j);
+        return __ldg(r + (size_t)(uint32_t)i * (uint32_t)ld + (uint32_t)j);
     }
 };
 
