@@ -306,7 +306,9 @@ def run_ours(args):
         try:
             import hashlib
             rec = json.load(open(prof))
-            src = open(os.path.join(ROOT, "paper_2502_05063_b300", "csrc", "apparent.cu"), "rb").read()
+            # the kernel's source: its file and the shared device helpers it inlines
+            src = b"".join(open(os.path.join(ROOT, "paper_2502_05063_b300", "csrc", f), "rb").read()
+                           for f in ("apparent.cu", "vr_common.cuh"))
             if rec.get("source_sha256") == hashlib.sha256(src).hexdigest():
                 traffic = rec.get("bytes_per_launch")
         except (OSError, ValueError):
