@@ -448,16 +448,18 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
         for (uint64_t i = threadIdx.x; i < hsz; i += HT) c.hkeys[i] = EMPTY;
         if (threadIdx.x == 0) *c.pool_used = 0;
         __syncthreads();
-        // 5a/5b. rounds over the unfinished columns: one warp each with a budget
-        // of additions that doubles per round, then finalization in order by the
-        // prefix-minimum rule; stop when all are final or a round makes no progress
+        // 5a/5b. one round over the columns, one warp each, without additions:
+        // it finds every pivot and settles, in order by the prefix-minimum rule,
+        // the columns whose pivot has no owner.  The rest go to the block engine,
+        // which on these clouds is faster than warp-engine additions (whole-
+        // column merges in global memory); more warp rounds cost time.
         uint32_t* ucur = ulist;
         uint32_t* unext = ulist + CCAP;
         for (int i = threadIdx.x; i < m; i += HT) ucur[i] = (uint32_t)i;
         int nu = m;
-        int budget = 8;
+        constexpr int budget = 0;
         __syncthreads();
-        while (nu > 0) {
+        if (nu > 0) {
             {
                 uint64_t* wst = A.wstage + (slot * HW + wid) * (int64_t)STAGE;
                 uint64_t* wa = A.wbuf + (slot * HW + wid) * (int64_t)(2 * WCAP);
@@ -529,10 +531,7 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
             }
             const int nn = M.carry_cnt;
             uint32_t* t = ucur; ucur = unext; unext = t;
-            const bool stalled = nn == nu;
             nu = nn;
-            if (stalled) break;
-            if (budget < (1 << 20)) budget *= 2;
         }
         VR_PHASE(5);
         // 5c. the remaining columns in order, each to completion (block engine)
@@ -548,11 +547,18 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
             bool ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, s);
             uint64_t key = EMPTY;
             unsigned long long col_adds = 0;
+            uint64_t prev = 0;  // pivot before the last addition
             int pre = 0;  // owner kind of the current pivot if probed during the last merge (3: none)
             while (ok) {
                 if (++col_adds > (1ull << 22)) { ok = false; break; }  // far beyond any column: flag the cloud
                 if (S.fsize == 0 && !heavy_refill<8>(S, back)) { key = EMPTY; break; }
                 key = S.buf[S.cur][0];
+                // A column finished here keeps no reduced form, so its owner's
+                // coboundary D_o stands in for R_o: a valid column operation, but
+                // one that may leave the pivot in place and then repeat forever.
+                // An unchanged pivot sends the cloud to the single-cloud path.
+                if (col_adds > 1 && key == prev) { ok = false; break; }
+                prev = key;
                 const int kind = pre ? (pre == 3 ? 0 : pre) : heavy_owner_probe<1>(c, S, key, self_key);
                 pre = 0;
                 if (kind == 0) break;

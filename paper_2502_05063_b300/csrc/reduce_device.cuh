@@ -338,7 +338,10 @@ __device__ void store_reduced(const Ctx& c, int64_t j, const uint64_t* W, int64_
     __syncwarp();
     if (lane == 0) {
         c.rc_off[j] = off;
-        c.rc_len[j] = fits ? (uint32_t)a : 0u;  // no room: later additions regenerate D_j
+        c.rc_len[j] = fits ? (uint32_t)a : 0u;
+        // without its reduced form a later column could only add D_j, which need
+        // not cancel the shared pivot: report the shortage instead
+        if (!fits) atomicExch(c.err, DEV_CAPACITY);
     }
 }
 
@@ -357,6 +360,7 @@ __device__ void reduce_one(const Ctx& c, int64_t j, int budget, uint64_t* stage,
     if (lane == 0) c.rc_len[j] = 0;
     if (piv == EMPTY) { out_key = EMPTY; out_status = ST_COMPLETE; return; }
     if (!warp_owner<P>(c, piv, self_key, o, opos)) { out_key = piv; out_status = ST_COMPLETE; return; }
+    if (budget <= 0) { out_key = piv; out_status = ST_BUDGET; return; }  // the pivot has an owner: not settled here
     uint64_t* W = bufA;
     uint64_t* spare = bufB;
     int64_t a = warp_add_coboundary<P>(c, s, stage, W, spare, 0, cap);
