@@ -35,7 +35,8 @@
 // reduced form.  The first unfinished column can never be blocked, so every
 // round makes progress (it is finalized or gains its additions); if the
 // first column overflows its back buffer in a batch of rounds, the remaining
-// columns restart with at least twice the room (VR_ERR_OOM past 2^31 rows).
+// columns restart in new buffers with at least twice the room (VR_ERR_OOM
+// past 2^31 rows) while finished columns keep theirs, with their reduced forms.
 //
 // Pivot lookup (the paper's two-layer store, Fig 5.10): first a device hash
 // of pivots found by this reduction, then the apparent pairs, which are not
@@ -174,7 +175,8 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
     HeavySmem& S = *reinterpret_cast<HeavySmem*>(hsm);
     const int64_t j = U[k];
     const int64_t slot = slot_of[j];
-    uint64_t* B = hs.B + slot * hs.bcap;
+    uint64_t* B = hs.B[slot];
+    const int64_t bcap = hs.bcap[slot];
     const uint64_t self_key = c.cols[j];
     Simplex<P> s;
     load_col<P>(c, self_key, s);
@@ -186,7 +188,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
         if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.holes = 0; S.Ks = EMPTY; S.cur = 0; }
         __syncthreads();
         adds = 0;
-        ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, s);
+        ok = heavy_add_coboundary<P>(c, S, B, bcap, s);
     } else {
         if (threadIdx.x == 0) {
             S.fsize = hs.fsize[slot]; S.bsize = hs.bsize[slot]; S.holes = hs.holes[slot]; S.Ks = hs.Ks[slot]; S.cur = 0;
@@ -227,17 +229,17 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
             const uint32_t os = slot_of[opos];
             if (os != 0xFFFFFFFFu && hs.init[os] && hs.adds[os] > 0) {
                 // owner finished by this engine: add its reduced form, front then back
-                ok = heavy_add_multiset(S, B, hs.bcap, hs.F + (int64_t)os * FC, hs.fsize[os]) &&
-                     heavy_add_multiset(S, B, hs.bcap, hs.B + (int64_t)os * hs.bcap, hs.bsize[os]);
+                ok = heavy_add_multiset(S, B, bcap, hs.F + (int64_t)os * FC, hs.fsize[os]) &&
+                     heavy_add_multiset(S, B, bcap, hs.B[os], hs.bsize[os]);
             } else if (c.rc_len[opos]) {
-                ok = heavy_add_stored(c, S, B, hs.bcap, opos);
+                ok = heavy_add_stored(c, S, B, bcap, opos);
             } else {
                 Simplex<P> o;
                 load_col<P>(c, c.cols[opos], o);
-                ok = heavy_add_coboundary<P>(c, S, B, hs.bcap, o);
+                ok = heavy_add_coboundary<P>(c, S, B, bcap, o);
             }
         } else {
-            const int r = heavy_apparent_add<P>(c, S, B, hs.bcap, self_key, &pre);
+            const int r = heavy_apparent_add<P>(c, S, B, bcap, self_key, &pre);
             if (r < 0) {  // s' is not apparent: the pivot has no owner, the column is complete
                 if (hs.prof && threadIdx.x == 0) S.tp[15] += clock64();
                 break;
@@ -313,11 +315,28 @@ k_reduce_heavy(Ctx c, Emit e, const uint32_t* __restrict__ U, const unsigned lon
     if (threadIdx.x == 0) *done = 0;  // ready for the next round (launched after this kernel ends)
 }
 
+// Slot k for column U[k], with the k-th back buffer of `arena` (bcap rows each).
 __global__ void k_assign_slots(const uint32_t* __restrict__ U, int64_t u, uint32_t* __restrict__ slot_of,
-                               uint8_t* __restrict__ init) {
+                               uint8_t* __restrict__ init, uint64_t* arena, int64_t bcap, uint64_t** B,
+                               int64_t* __restrict__ bc) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x) {
         slot_of[U[k]] = (uint32_t)k;
         init[k] = 0;
+        B[k] = arena + k * bcap;
+        bc[k] = bcap;
+    }
+}
+
+// Regrowth: the unfinished columns U[0..u) restart in the k-th buffer of a
+// new arena; finished columns keep their slots, buffers and reduced forms.
+__global__ void k_regrow_slots(const uint32_t* __restrict__ U, int64_t u, const uint32_t* __restrict__ slot_of,
+                               uint8_t* __restrict__ init, uint64_t* arena, int64_t bcap, uint64_t** B,
+                               int64_t* __restrict__ bc) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t slot = slot_of[U[k]];
+        init[slot] = 0;
+        B[slot] = arena + k * bcap;
+        bc[slot] = bcap;
     }
 }
 
@@ -387,9 +406,10 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         HeavyState h;
         // back buffers share an arena of 2^28 rows (2 GB; VR_HEAVY_ARENA_LOG2 overrides, for tests)
         const int64_t arena = heavy_arena_rows();
-        h.bcap = std::max<int64_t>((int64_t)1 << 16, std::min<int64_t>((int64_t)1 << 22, arena / nslot));
+        int64_t bcap = std::max<int64_t>((int64_t)1 << 16, std::min<int64_t>((int64_t)1 << 22, arena / nslot)) & ~(int64_t)15;
         h.F = ws.alloc_n<uint64_t>((size_t)nslot * FC);
-        h.B = ws.alloc_n<uint64_t>((size_t)nslot * h.bcap);
+        h.B = ws.alloc_n<uint64_t*>(nslot);
+        h.bcap = ws.alloc_n<int64_t>(nslot);
         h.Ks = ws.alloc_n<uint64_t>(nslot);
         h.fsize = ws.alloc_n<int32_t>(nslot);
         h.bsize = ws.alloc_n<int64_t>(nslot);
@@ -399,7 +419,8 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         h.prof = log_enabled() ? ws.zeros_n<unsigned long long>(8) : nullptr;
         uint32_t* slot_of = ws.alloc_n<uint32_t>(m);
         VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));  // no slot: phase-1 columns
-        k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
+        k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(
+            U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)nslot * bcap), bcap, h.B, h.bcap);
         int budget = 64;
         // Columns are finalized between rounds only, so a round that runs as
         // long as its longest column would keep columns it unblocks idle; a
@@ -450,7 +471,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 fprintf(stderr,
                         "[vr] dim%d block round %d: budget %d bcap %lld: %lld -> %lld unfinished; %.3f ms, "
                         "max additions %lld, max block cycles %lld\n",
-                        P, rounds, budget, (long long)h.bcap, (long long)u0, (long long)un, ms, (long long)hs.p[24],
+                        P, rounds, budget, (long long)bcap, (long long)u0, (long long)un, ms, (long long)hs.p[24],
                         (long long)hs.p[25]);
             }
             const bool stalled = un == u0;
@@ -462,13 +483,14 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 // back buffer in this batch: the remaining columns restart from
                 // scratch with at least twice the room (the whole arena when
                 // that is more), up to 2^31 rows in all
-                const int64_t nb = std::max<int64_t>(2 * h.bcap, arena / u) & ~(int64_t)15;
+                const int64_t nb = std::max<int64_t>(2 * bcap, arena / u) & ~(int64_t)15;
                 if ((double)nb * (double)u > (double)((int64_t)1 << 31)) throw Error{VR_ERR_OOM};
-                h.bcap = nb;
-                h.B = ws.alloc_n<uint64_t>((size_t)u * h.bcap);
-                // slots are reassigned: finished columns lose their stored forms
-                VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));
-                k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(U, u, slot_of, h.init);
+                bcap = nb;
+                if (log_enabled())
+                    fprintf(stderr, "[vr] dim%d regrowth: %lld unfinished columns restart with %lld rows each\n", P,
+                            (long long)u, (long long)bcap);
+                k_regrow_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(
+                    U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)u * bcap), bcap, h.B, h.bcap);
                 VR_CUDA(cudaGetLastError());
             }
         }

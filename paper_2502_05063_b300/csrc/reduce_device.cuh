@@ -460,8 +460,8 @@ static_assert(FC < (1 << 16) && HSTAGE < (1 << 16), "merge splits pack two 16-bi
 
 struct HeavyState {
     uint64_t* F;       // slots x FC, the front saved between rounds
-    uint64_t* B;       // slots x bcap
-    int64_t bcap;
+    uint64_t** B;      // per slot: its back buffer (a regrowth moves the unfinished columns'
+    int64_t* bcap;     // buffers; a finished column keeps its reduced form) and its rows
     uint64_t* Ks;      // per slot
     int32_t* fsize;
     int64_t* bsize;

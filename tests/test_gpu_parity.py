@@ -254,14 +254,17 @@ def test_workload_golden(vr, name):
             assert bc.stats[p]["essential"] == g["essential"][p]
 
 
-def test_back_buffer_regrowth_matches_golden(vr):
+@pytest.mark.parametrize("arena_log2", [16, 21])
+def test_back_buffer_regrowth_matches_golden(vr, arena_log2):
     """Columns whose back buffers overflow restart with more room; the pairing is unchanged.
 
-    With a 2^21-row arena for the block engine's back buffers (64K rows per
-    column) the long cocycle columns of torus500 (several 100K rows) overflow
-    again and again; each overflow of the first unfinished column, in any
-    round of a batch, must enlarge the buffers.  Runs in a child process,
-    which reads the arena size from its environment.
+    With a 2^16- or 2^21-row arena for the block engine's back buffers (64K
+    rows per column) the long cocycle columns of torus500 (several 100K rows)
+    overflow again and again; each overflow of the first unfinished column,
+    in any round of a batch, must enlarge the buffers, and columns finished
+    before a regrowth keep their reduced forms for the columns they own
+    pivots of.  Runs in a child process, which reads the arena size from its
+    environment.
     """
     here = os.path.dirname(os.path.abspath(__file__))
     script = (
@@ -273,7 +276,7 @@ def test_back_buffer_regrowth_matches_golden(vr):
         "bc = vr.barcodes(points=pts, dmax=g['dmax'], threshold=thr)\n"
         "bad = [p for p in range(g['dmax'] + 1) if rows_gpu(bc, p) != dg[p]]\n"
         "print('MISMATCH' if bad else 'OK', bad)\n" % (os.path.dirname(here), here))
-    env = dict(os.environ, VR_HEAVY_ARENA_LOG2="21")
+    env = dict(os.environ, VR_HEAVY_ARENA_LOG2=str(arena_log2))
     out = subprocess.run([sys.executable, "-c", script], env=env, capture_output=True, text=True, timeout=900)
     assert out.returncode == 0, out.stderr[-3000:]
     assert out.stdout.strip().startswith("OK"), out.stdout
