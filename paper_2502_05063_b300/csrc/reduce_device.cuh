@@ -742,12 +742,16 @@ __device__ void heavy_compact_back(HeavySmem& S, uint64_t* B) {
 }
 
 // Refill an empty front from B.  Returns false if the column is zero.
-// The split T comes from a sorted sample of B (its quantile for about
-// 0.7 FKEEP rows); one pass over B collects the positions of the rows below
-// T (at most FC of them, else T is lowered and the pass repeated), then
-// those rows are gathered, replaced by holes (EMPTY, above every row key),
-// sorted, and the rows of odd multiplicity become the front (Z/2).  B is
-// only read in full; it is compacted once holes make up half of it.
+// Two splits Ta < Tb come from a sorted sample of B (its quantiles for
+// about 0.45 FC and 0.83 FC rows).  One pass over B collects the positions
+// of the rows below Tb (room for 2 FC); if they fit the front they are
+// taken, else, if the rows below Ta among them do, those are -- so a
+// refill takes close to a full front without a second pass over B (a pass
+// costs the same for either, and fewer, larger refills are cheaper).  If
+// neither fits, the splits move and the pass repeats.  The rows are
+// gathered, replaced by holes (EMPTY, above every row key), sorted, and the
+// rows of odd multiplicity become the front (Z/2).  B is only read in
+// full; it is compacted once holes make up half of it.
 // UN: rows each thread loads per step of the pass (independent loads in flight).
 template <int UN = 16>
 __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
@@ -762,30 +766,34 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
         if (bsz == 0) return false;
         HPROF_T0();
         if (threadIdx.x == 0) { atomicAdd(&g_heavy_counts[0], 1ull); S.tp[9] += 1; }
-        uint64_t* Sm = S.buf[S.cur];       // the sample (the front is empty)
-        uint64_t* G = S.buf[S.cur ^ 1];    // positions, then rows, below T
-        uint64_t T = EMPTY;
-        int q = 0;
+        uint64_t* Sm = S.buf[S.cur];  // the sample (the front is empty), then the gathered rows
+        uint32_t* P = reinterpret_cast<uint32_t*>(S.buf[S.cur ^ 1]);  // positions of the rows below Tb (2 FC)
+        uint64_t Ta = EMPTY, Tb = EMPTY;
+        int qa = 0, qb = 0;
         if (bsz > (FKEEP * 7) / 10) {
             const int64_t stride = bsz / NS;
             for (int i = threadIdx.x; i < NS; i += HT) Sm[i] = B[(int64_t)i * stride];
             __syncthreads();
             block_bitonic(Sm, NS);
-            q = (int)((double)FKEEP * 0.7 * NS / (double)bsz);
-            if (q < 1) q = 1;
-            if (q > NS - 1) q = NS - 1;
-            T = Sm[q];
+            qa = (int)((double)FC * 0.45 * NS / (double)bsz);
+            qb = (int)((double)FC * 0.83 * NS / (double)bsz);
+            qa = qa < 1 ? 1 : (qa > NS - 2 ? NS - 2 : qa);
+            qb = qb <= qa ? qa + 1 : (qb > NS - 1 ? NS - 1 : qb);
+            Ta = Sm[qa];
+            Tb = Sm[qb];
         }
         HPROF_LAP(4);
-        // 2. positions of the rows below T (one pass; the smallest row is only
-        //    looked for when T has to be lowered to it)
-        int cnt;
+        // 2. positions of the rows below Tb (one pass; the smallest row is
+        //    only looked for when the splits must drop to it)
+        int cnt, nsel = 0;
+        bool filtered = false;
+        uint64_t T = Tb;
         uint64_t bmin = EMPTY;
         bool have_min = false;
         for (;;) {
             if (threadIdx.x == 0) cnt_sh = 0;
             __syncthreads();
-            // UN rows per thread per step; a mask of the rows below T, and the
+            // UN rows per thread per step; a mask of the rows below Tb, and the
             // rare hits placed by one shared-memory atomic per lane
             for (int64_t w0 = threadIdx.x; w0 < bsz; w0 += (int64_t)HT * UN) {
                 uint64_t kk[UN];
@@ -796,13 +804,13 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
                 }
                 uint32_t mask = 0;
 #pragma unroll
-                for (int u = 0; u < UN; ++u) mask |= (uint32_t)(kk[u] < T) << u;
+                for (int u = 0; u < UN; ++u) mask |= (uint32_t)(kk[u] < Tb) << u;
                 if (mask) {
                     int slot = atomicAdd(&cnt_sh, __popc(mask));
 #pragma unroll
                     for (int u = 0; u < UN; ++u)
                         if ((mask >> u) & 1u) {
-                            if (slot < FC) G[slot] = (uint64_t)(w0 + (int64_t)u * HT);
+                            if (slot < 2 * FC) P[slot] = (uint32_t)(w0 + (int64_t)u * HT);
                             ++slot;
                         }
                 }
@@ -810,8 +818,17 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
             __syncthreads();
             cnt = cnt_sh;
             __syncthreads();
-            if (cnt >= 1 && cnt <= FC) break;
-            if (cnt > FC && have_min && T == bmin + 1) break;  // one key with more copies than fit
+            if (cnt >= 1 && cnt <= FC) { T = Tb; nsel = cnt; break; }
+            int ca = -1;  // rows below Ta, when known
+            if (cnt > FC && cnt <= 2 * FC && Ta < Tb) {
+                int c = 0;
+                for (int i = threadIdx.x; i < cnt; i += HT) c += B[P[i]] < Ta;
+                int tot;
+                block_excl_scan(c, S.ws, &tot);
+                ca = tot;
+                if (ca >= 1 && ca <= FC) { T = Ta; nsel = ca; filtered = true; break; }
+            }
+            if (cnt > FC && have_min && Tb == bmin + 1) { T = Tb; nsel = cnt; break; }  // one key, more copies than fit
             if (!have_min) {
                 if (threadIdx.x == 0) min_sh = EMPTY;
                 __syncthreads();
@@ -836,64 +853,87 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
                     return false;
                 }
             }
-            if (cnt == 0 || q <= 1) {
-                T = bmin + 1;  // the smallest key alone
+            if (ca == 0 && qb - qa > 1) {  // Ta too low, Tb too high: split the difference
+                qb = (qa + qb) >> 1;
+                Tb = Sm[qb];
+            } else if (cnt == 0 || qa <= 1) {
+                Ta = bmin + 1;  // the smallest key alone
+                Tb = Ta;
+                qa = qb = 0;
             } else {
-                q >>= 1;
-                T = Sm[q];
+                qb = qa;
+                Tb = Ta;
+                qa >>= 1;
+                Ta = Sm[qa];
             }
         }
         HPROF_LAP(5);
-        if (cnt > FC) {  // every copy of bmin becomes a hole; its parity decides
+        if (nsel > FC) {  // every copy of bmin becomes a hole; its parity decides
             for (int64_t i = threadIdx.x; i < bsz; i += HT)
                 if (B[i] == bmin) B[i] = EMPTY;
             __syncthreads();
             if (threadIdx.x == 0) {
                 S.buf[S.cur][0] = bmin;
-                S.fsize = cnt & 1;
+                S.fsize = nsel & 1;
                 S.Ks = T;
             }
             __syncthreads();
         } else {
-            // gather the rows and leave holes
-            for (int i = threadIdx.x; i < cnt; i += HT) {
-                const int64_t pos = (int64_t)G[i];
-                G[i] = B[pos];
-                B[pos] = EMPTY;
+            // gather the rows into the sample's buffer and leave holes
+            if (!filtered) {
+                for (int i = threadIdx.x; i < nsel; i += HT) {
+                    const int64_t pos = (int64_t)P[i];
+                    Sm[i] = B[pos];
+                    B[pos] = EMPTY;
+                }
+            } else {  // the rows below Ta among those below Tb
+                int c = 0;
+                for (int i = threadIdx.x; i < cnt; i += HT) c += B[P[i]] < Ta;
+                int tot;
+                int o = block_excl_scan(c, S.ws, &tot);
+                for (int i = threadIdx.x; i < cnt; i += HT) {
+                    const int64_t pos = (int64_t)P[i];
+                    const uint64_t k = B[pos];
+                    if (k < Ta) {
+                        Sm[o++] = k;
+                        B[pos] = EMPTY;
+                    }
+                }
             }
             int len = 1;
-            while (len < cnt) len <<= 1;
-            for (int i = cnt + threadIdx.x; i < len; i += HT) G[i] = EMPTY;
+            while (len < nsel) len <<= 1;
+            for (int i = nsel + threadIdx.x; i < len; i += HT) Sm[i] = EMPTY;
             __syncthreads();
             HPROF_LAP(6);
-            block_bitonic(G, len);
-            // keep the rows of odd multiplicity
-            uint64_t* F = S.buf[S.cur];
-            const int chunk = (cnt + HT - 1) / HT;
-            const int c0 = min(cnt, (int)threadIdx.x * chunk), c1 = min(cnt, c0 + chunk);
+            block_bitonic(Sm, len);
+            // keep the rows of odd multiplicity, in the other buffer
+            uint64_t* F = S.buf[S.cur ^ 1];
+            const int chunk = (nsel + HT - 1) / HT;
+            const int c0 = min(nsel, (int)threadIdx.x * chunk), c1 = min(nsel, c0 + chunk);
             int keep = 0;
             for (int i = c0; i < c1; ++i) {
-                if (i > 0 && G[i - 1] == G[i]) continue;
+                if (i > 0 && Sm[i - 1] == Sm[i]) continue;
                 int e = i;
-                while (e + 1 < cnt && G[e + 1] == G[i]) ++e;
+                while (e + 1 < nsel && Sm[e + 1] == Sm[i]) ++e;
                 keep += ((e - i + 1) & 1);
             }
             int tk;
-            int pos = block_excl_scan(keep, S.ws, &tk);
+            int pos = block_excl_scan(keep, S.ws, &tk);  // its barriers: every position was read
             for (int i = c0; i < c1; ++i) {
-                if (i > 0 && G[i - 1] == G[i]) continue;
+                if (i > 0 && Sm[i - 1] == Sm[i]) continue;
                 int e = i;
-                while (e + 1 < cnt && G[e + 1] == G[i]) ++e;
-                if ((e - i + 1) & 1) F[pos++] = G[i];
+                while (e + 1 < nsel && Sm[e + 1] == Sm[i]) ++e;
+                if ((e - i + 1) & 1) F[pos++] = Sm[i];
             }
             __syncthreads();
             if (threadIdx.x == 0) {
+                S.cur ^= 1;
                 S.fsize = tk;
                 S.Ks = T;
             }
             __syncthreads();
         }
-        const int64_t holes = S.holes + cnt;
+        const int64_t holes = S.holes + nsel;
         if (holes == bsz) {
             if (threadIdx.x == 0) { S.bsize = 0; S.holes = 0; }
             __syncthreads();
