@@ -45,7 +45,6 @@ constexpr int HCAP = 16384;            // hash slots per cloud (power of two, >=
 constexpr int64_t BACKCAP = 1 << 20;   // back rows of the block engine per cloud (8 MB)
 constexpr int EDGE_BITS = 15;          // C(256,2) - 1 < 2^15
 constexpr int TRI_BITS = 22;           // C(256,3) - 1 < 2^22
-constexpr int WCAP = 2048;             // per-warp working column of the first pass
 constexpr int64_t POOLCAP = 1 << 15;   // stored reduced columns per cloud
 
 struct BatchArgs {
@@ -69,7 +68,6 @@ struct BatchArgs {
     PairRec* h1tmp;
     uint64_t* back;
     uint64_t* wstage;      // slots x HW x STAGE
-    uint64_t* wbuf;        // slots x HW x 2 x WCAP
     uint64_t* pool;        // slots x POOLCAP
     unsigned long long* pool_used;  // per slot
     uint64_t* rc_off;      // slots x CCAP
@@ -450,9 +448,8 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
         __syncthreads();
         // 5a/5b. one round over the columns, one warp each, without additions:
         // it finds every pivot and settles, in order by the prefix-minimum rule,
-        // the columns whose pivot has no owner.  The rest go to the block engine,
-        // which on these clouds is faster than warp-engine additions (whole-
-        // column merges in global memory); more warp rounds cost time.
+        // the columns whose pivot has no owner.  The rest go to the block engine
+        // (measured faster on these clouds than more warp rounds).
         uint32_t* ucur = ulist;
         uint32_t* unext = ulist + CCAP;
         for (int i = threadIdx.x; i < m; i += HT) ucur[i] = (uint32_t)i;
@@ -462,13 +459,12 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
         if (nu > 0) {
             {
                 uint64_t* wst = A.wstage + (slot * HW + wid) * (int64_t)STAGE;
-                uint64_t* wa = A.wbuf + (slot * HW + wid) * (int64_t)(2 * WCAP);
                 for (int q = wid; q < nu; q += HW) {
                     const int j = ucur[q];
                     uint64_t key;
                     uint8_t st;
                     uint32_t ad;
-                    reduce_one<1>(c, j, budget, wst, wa, wa + WCAP, WCAP, key, st, ad);
+                    reduce_one<1>(c, j, budget, wst, key, st, ad);
                     if (lane == 0) { cur_key[j] = key; status[j] = st; adds_j[j] = ad; }
                 }
             }
@@ -565,7 +561,7 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
                 if (kind == 1) {
                     const int64_t opos = S.opos;
                     if (c.rc_len[opos]) {
-                        ok = heavy_add_stored(c, S, back, BACKCAP, opos);
+                        ok = heavy_add_stored<1>(c, S, back, BACKCAP, opos);
                     } else {
                         Simplex<1> o;
                         load_col<1>(c, cols[opos], o);
@@ -711,7 +707,7 @@ std::map<std::pair<int, int64_t>, int> g_tuned;  // (device, mean-size bucket) -
 size_t slot_bytes() {
     return (size_t)BMAXN * BLD * 4 + (size_t)HCAP * 12 +
            (size_t)CCAP * (8 + 8 + 1 + 8 + sizeof(PairRec) + 8 + 4 + 4) + (size_t)BACKCAP * 8 +
-           (size_t)HW * STAGE * 8 + (size_t)HW * 2 * WCAP * 8 + (size_t)POOLCAP * 8 + 16 * 256;
+           (size_t)HW * STAGE * 8 + (size_t)POOLCAP * 8 + 16 * 256;
 }
 
 void free_plan(BatchPlan* p) {
@@ -771,7 +767,6 @@ BatchPlan* make_plan(int dev, int num, int dim, int dmax, int want_edges, int th
         A.h1tmp = carve<PairRec>(cur, (size_t)slots * CCAP);
         A.back = carve<uint64_t>(cur, (size_t)slots * BACKCAP);
         A.wstage = carve<uint64_t>(cur, (size_t)slots * HW * STAGE);
-        A.wbuf = carve<uint64_t>(cur, (size_t)slots * HW * 2 * WCAP);
         A.pool = carve<uint64_t>(cur, (size_t)slots * POOLCAP);
         A.pool_used = carve<unsigned long long>(cur, (size_t)slots);
         A.rc_off = carve<uint64_t>(cur, (size_t)slots * CCAP);

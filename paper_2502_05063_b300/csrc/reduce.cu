@@ -26,8 +26,10 @@
 // strictly decreasing keys, hence distinct pivots.
 //
 // Phase 1: one warp per column, at most 8 additions (none when there are
-// at most four columns per SM), all columns at once; finished columns that
-// needed additions keep their reduced form.  Phase 2:
+// at most four columns per SM), all columns at once.  No column is final
+// yet, so every owner is apparent; a column is kept as the list of
+// simplices added to it (see reduce_one), and finished columns that needed
+// additions store that list, their column of V.  Phase 2:
 // one block per remaining column (the front/back engine of
 // reduce_device.cuh), state kept across rounds, at most 64 additions per
 // round so that finalized pivots reach waiting columns early; a column
@@ -59,13 +61,9 @@ namespace {
 template <int P>
 __global__ void __launch_bounds__(RED_WARPS * 32)
 k_reduce_round(Ctx c, const uint32_t* __restrict__ U, int64_t u, int budget, uint64_t* __restrict__ cur_key,
-               uint8_t* __restrict__ status, uint32_t* __restrict__ adds, uint64_t* __restrict__ scratch,
-               int64_t cap, unsigned long long* __restrict__ work) {
+               uint8_t* __restrict__ status, uint32_t* __restrict__ adds, unsigned long long* __restrict__ work) {
     __shared__ uint64_t stage_all[RED_WARPS][STAGE];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t slot = (int64_t)blockIdx.x * RED_WARPS + wid;
-    uint64_t* bufA = scratch + slot * 2 * cap;
-    uint64_t* bufB = bufA + cap;
     for (;;) {
         unsigned long long k = 0;
         if (lane == 0) k = atomicAdd(work, 1ull);
@@ -75,7 +73,7 @@ k_reduce_round(Ctx c, const uint32_t* __restrict__ U, int64_t u, int budget, uin
         uint64_t key;
         uint8_t st;
         uint32_t ad;
-        reduce_one<P>(c, j, budget, stage_all[wid], bufA, bufB, cap, key, st, ad);
+        reduce_one<P>(c, j, budget, stage_all[wid], key, st, ad);
         if (lane == 0) { cur_key[j] = key; status[j] = st; adds[j] = ad; }
     }
 }
@@ -232,7 +230,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
                 ok = heavy_add_multiset(S, B, bcap, hs.F + (int64_t)os * FC, hs.fsize[os]) &&
                      heavy_add_multiset(S, B, bcap, hs.B[os], hs.bsize[os]);
             } else if (c.rc_len[opos]) {
-                ok = heavy_add_stored(c, S, B, bcap, opos);
+                ok = heavy_add_stored<P>(c, S, B, bcap, opos);
             } else {
                 Simplex<P> o;
                 load_col<P>(c, c.cols[opos], o);
@@ -371,8 +369,6 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         const int64_t max_slots = 148 * 4 * RED_WARPS;
         int64_t slots = u < max_slots ? u : max_slots;
         slots = (slots + RED_WARPS - 1) / RED_WARPS * RED_WARPS;
-        const int64_t cap = 8192;
-        uint64_t* scratch = ws.alloc_n<uint64_t>((size_t)slots * 2 * cap);
         VR_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s));
         // Phase 1 is a throughput engine for many short columns; with at most
         // four columns per SM the block engine takes every column at once, and
@@ -385,7 +381,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         }
         const int p1_budget = u <= 4 * (int64_t)sms ? 0 : 8;
         k_reduce_round<P><<<(unsigned)(slots / RED_WARPS), RED_WARPS * 32, 0, s>>>(c, U, u, p1_budget, cur_key, status,
-                                                                                   adds, scratch, cap, ctr);
+                                                                                   adds, ctr);
         k_finalize<<<1, 1024, 0, s>>>(c, e, U, u, cur_key, status, adds, Un, ctr + 1, ctr + 2);
         VR_CUDA(cudaGetLastError());
         VR_CUDA(cudaMemcpyAsync(&hs.p[8], ctr + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -516,7 +512,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
     if (log_enabled()) {
         VR_CUDA(cudaMemcpyAsync(&hs.p[10], c.pool_used, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         VR_CUDA(cudaStreamSynchronize(s));
-        fprintf(stderr, "[vr] dim%d reduction: %d block rounds, stored rows %lld of %lld\n", P, rounds,
+        fprintf(stderr, "[vr] dim%d reduction: %d block rounds, stored generators %lld of %lld\n", P, rounds,
                 (long long)hs.p[10], (long long)c.pool_cap);
     }
 }
@@ -543,7 +539,7 @@ void run_reduction(const ReduceIn& in, const ReduceOut& out, bool keep_zero, Wor
     VR_CUDA(cudaMemsetAsync(c.hkeys, 0xFF, hcap * sizeof(uint64_t), ws.stream));
     c.hmask = hcap - 1;
     c.err = out.dev_err;
-    c.pool_cap = std::min<int64_t>((int64_t)1 << 24, std::max<int64_t>((int64_t)1 << 16, in.num_cols * 2048));
+    c.pool_cap = in.num_cols * RGEN;  // a column stores at most RGEN generators, once
     c.pool = ws.alloc_n<uint64_t>((size_t)c.pool_cap);
     c.pool_used = ws.zeros_n<unsigned long long>(1);
     c.rc_off = ws.alloc_n<uint64_t>((size_t)in.num_cols);

@@ -84,35 +84,6 @@ __device__ __forceinline__ uint64_t row_key(const Ctx& c, const Simplex<P>& s, i
     return ((uint64_t)rt << c.rcb) | (c.rcmask - cofacet_cidx<P>(c.B, s.v, w));
 }
 
-// Pivot of the unreduced column D_s: smallest (rank asc, w desc) cofacet.
-template <int P>
-__device__ uint64_t warp_column_pivot(const Ctx& c, const Simplex<P>& s) {
-    const int lane = threadIdx.x & 31;
-    const int64_t n = c.R.n;
-    uint32_t brt = 0xFFFFFFFFu;
-    int64_t bw = -1;
-    for (int64_t base = n - 1; base >= 0; base -= 32) {
-        const int64_t w = base - lane;
-        bool ok = w >= 0;
-#pragma unroll
-        for (int a = 0; a <= P; ++a) ok = ok && (w != s.v[a]);
-        if (ok) {
-            uint32_t rt = s.r;
-#pragma unroll
-            for (int a = 0; a <= P; ++a) rt = max(rt, c.R(s.v[a], w));
-            if (rt <= c.thr && rt < brt) { brt = rt; bw = w; }  // w only decreases per lane
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        uint32_t ort = __shfl_xor_sync(0xffffffffu, brt, o);
-        int64_t ow = __shfl_xor_sync(0xffffffffu, bw, o);
-        if (ort < brt || (ort == brt && ow > bw)) { brt = ort; bw = ow; }
-    }
-    if (bw < 0) return EMPTY;
-    return row_key<P>(c, s, bw, brt);
-}
-
 // Bitonic sort of stage[0..len) (len a power of two >= 32) by one warp.
 __device__ void warp_bitonic(uint64_t* stage, int len) {
     const int lane = threadIdx.x & 31;
@@ -139,93 +110,62 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t le
     return lo;
 }
 
-// out = in XOR S (symmetric difference of two sorted sets), returns the new
-// size or -1 if it would exceed cap.
-__device__ int64_t warp_xor_merge(const uint64_t* in, int64_t a, const uint64_t* S, int64_t b, uint64_t* out,
-                                  int64_t cap) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    int64_t matched = 0;
-    bool over = false;
-    for (int64_t base = 0; base < a; base += 32) {
-        const int64_t i = base + lane;
-        const uint64_t x = i < a ? in[i] : EMPTY;
-        int64_t bs = 0;
-        bool m = false;
-        if (i < a) {
-            bs = lower_bound_u64(S, b, x);
-            m = bs < b && S[bs] == x;
-        }
-        const uint32_t mb = __ballot_sync(0xffffffffu, m);
-        const int64_t mw = matched + __popc(mb & lt);
-        if (i < a && !m) {
-            const int64_t pos = i + bs - 2 * mw;
-            if (pos < cap) out[pos] = x; else over = true;
-        }
-        matched += __popc(mb);
-    }
-    int64_t matched2 = 0;
-    for (int64_t base = 0; base < b; base += 32) {
-        const int64_t k = base + lane;
-        const uint64_t y = k < b ? S[k] : EMPTY;
-        int64_t bw = 0;
-        bool m = false;
-        if (k < b) {
-            bw = lower_bound_u64(in, a, y);
-            m = bw < a && in[bw] == y;
-        }
-        const uint32_t mb = __ballot_sync(0xffffffffu, m);
-        const int64_t ms = matched2 + __popc(mb & lt);
-        if (k < b && !m) {
-            const int64_t pos = k + bw - 2 * ms;
-            if (pos < cap) out[pos] = y; else over = true;
-        }
-        matched2 += __popc(mb);
-    }
-    __syncwarp();
-    if (__any_sync(0xffffffffu, over)) return -1;
-    return a + b - 2 * matched;
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
+    const uint32_t hi = __reduce_min_sync(0xffffffffu, (uint32_t)(x >> 32));
+    const uint32_t lo = __reduce_min_sync(0xffffffffu, (uint32_t)(x >> 32) == hi ? (uint32_t)x : 0xffffffffu);
+    return ((uint64_t)hi << 32) | lo;
 }
 
-// W <- W + D_x.  W lives in *W (size a) and the spare buffer *spare; the
-// pointers are swapped as pieces are merged.  Returns the new size or -1.
-template <int P>
-__device__ int64_t warp_add_coboundary(const Ctx& c, const Simplex<P>& x, uint64_t* stage, uint64_t*& W,
-                                       uint64_t*& spare, int64_t a, int64_t cap) {
+// The K smallest row keys of D_x above `cut` (all rows if !has_cut), in
+// ascending order, EMPTY-padded, by one warp: the cofacets x + {w} one lane
+// each, every lane keeping its K smallest in registers (a key and its
+// binomial reads only when its diameter rank can still enter), then K
+// rounds of a warp minimum, the lane holding it moving on.  Every lane
+// returns the same out[].
+constexpr int RC = 4;
+template <int P, int K = RC>
+__device__ void warp_rows_above(const Ctx& c, const Simplex<P>& x, bool has_cut, uint64_t cut, uint64_t* out) {
+    constexpr int RC = K;
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
     const int64_t n = c.R.n;
-    int64_t base = n - 1;
-    while (base >= 0) {
-        int fill = 0;
-        while (base >= 0 && fill <= STAGE - 32) {
-            const int64_t w = base - lane;
-            bool ok = w >= 0;
+    const uint32_t rcut = has_cut ? (uint32_t)(cut >> c.rcb) : 0u;
+    uint64_t t[RC];
 #pragma unroll
-            for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
+    for (int r = 0; r < RC; ++r) t[r] = EMPTY;
+    for (int64_t base = n - 1; base >= 0; base -= 32) {
+        const int64_t w = base - lane;
+        bool ok = w >= 0;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
+        if (ok) {
             uint32_t rt = x.r;
-            if (ok) {
 #pragma unroll
-                for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
-                ok = rt <= c.thr;
+            for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
+            if (rt <= c.thr && rt >= rcut && ((uint64_t)rt << c.rcb) <= t[RC - 1]) {
+                uint64_t key = row_key<P>(c, x, w, rt);
+                if ((!has_cut || key > cut) && key < t[RC - 1]) {
+                    t[RC - 1] = key;
+#pragma unroll
+                    for (int r = RC - 1; r > 0; --r) {
+                        const uint64_t lo = t[r - 1] < t[r] ? t[r - 1] : t[r], hi = t[r - 1] < t[r] ? t[r] : t[r - 1];
+                        t[r - 1] = lo;
+                        t[r] = hi;
+                    }
+                }
             }
-            const uint32_t b = __ballot_sync(0xffffffffu, ok);
-            if (ok) stage[fill + __popc(b & lt)] = row_key<P>(c, x, w, rt);
-            fill += __popc(b);
-            base -= 32;
         }
-        int len = 32;
-        while (len < fill) len <<= 1;
-        for (int i = fill + lane; i < len; i += 32) stage[i] = EMPTY;
-        __syncwarp();
-        warp_bitonic(stage, len);
-        const int64_t na = warp_xor_merge(W, a, stage, fill, spare, cap);
-        __syncwarp();
-        if (na < 0) return -1;
-        uint64_t* t = W; W = spare; spare = t;
-        a = na;
     }
-    return a;
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+        const uint64_t m = warp_min_u64(t[0]);
+        out[r] = m;
+        const uint32_t own = __ballot_sync(0xffffffffu, m != EMPTY && t[0] == m);
+        if (own && lane == __ffs(own) - 1) {  // keys of one coboundary are distinct: one owner
+#pragma unroll
+            for (int q = 0; q < RC - 1; ++q) t[q] = t[q + 1];
+            t[RC - 1] = EMPTY;
+        }
+    }
 }
 
 // Position of the finished column whose pivot is the (p+1)-simplex ct, or -1;
@@ -308,77 +248,118 @@ __device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex
     return true;
 }
 
-// W <- W + R_o: the stored reduced column of a finished column, or its
-// coboundary when none is stored (apparent columns, zero-addition columns).
+// Keep the reduced column of position j as the list of simplices whose
+// coboundaries add up to it (its column of V: R_j = D_j + sum of D_g), as
+// column keys, for later additions.
 template <int P>
-__device__ int64_t warp_add_owner(const Ctx& c, const Simplex<P>& o, int64_t opos, uint64_t* stage, uint64_t*& W,
-                                  uint64_t*& spare, int64_t a, int64_t cap) {
-    if (opos >= 0) {
-        const uint32_t len = c.rc_len[opos];
-        if (len) {
-            const int64_t na = warp_xor_merge(W, a, c.pool + c.rc_off[opos], len, spare, cap);
-            __syncwarp();
-            if (na < 0) return -1;
-            uint64_t* t = W; W = spare; spare = t;
-            return na;
-        }
-    }
-    return warp_add_coboundary<P>(c, o, stage, W, spare, a, cap);
-}
-
-// Keep the reduced column of position j (W[0..a)) for later additions.
-__device__ void store_reduced(const Ctx& c, int64_t j, const uint64_t* W, int64_t a) {
+__device__ void store_generators(const Ctx& c, int64_t j, const Simplex<P>* gs, int m) {
     const int lane = threadIdx.x & 31;
     unsigned long long off = 0;
-    if (lane == 0) off = atomicAdd(c.pool_used, (unsigned long long)a);
+    if (lane == 0) off = atomicAdd(c.pool_used, (unsigned long long)m);
     off = __shfl_sync(0xffffffffu, off, 0);
-    const bool fits = (int64_t)(off + a) <= c.pool_cap && a <= 0xFFFFFFFFll;
-    if (fits)
-        for (int64_t i = lane; i < a; i += 32) c.pool[off + i] = W[i];
+    const bool fits = (int64_t)(off + m) <= c.pool_cap;
+    if (fits && lane < m) c.pool[off + lane] = col_key<P>(c, gs[lane]);
     __syncwarp();
     if (lane == 0) {
         c.rc_off[j] = off;
-        c.rc_len[j] = fits ? (uint32_t)a : 0u;
+        c.rc_len[j] = fits ? (uint32_t)m : 0u;
         // without its reduced form a later column could only add D_j, which need
         // not cancel the shared pivot: report the shortage instead
         if (!fits) atomicExch(c.err, DEV_CAPACITY);
     }
 }
 
-// Reduce column j (position in cols) against the known pivots.  At most
-// `budget` additions; on completion with additions the result is stored.
+// Reduce column j (position in cols) against the known pivots, with at most
+// `budget` additions (and at most RGEN - 1).  The column is kept implicitly
+// as its generators g (j itself and the owners added so far): a row r has
+// multiplicity #{g : g is a facet of r}, and each generator caches the RC
+// smallest rows of D_g above the rows already known to cancel.  The pivot
+// is the smallest current row if it occurs an odd number of times;
+// otherwise it cancels, the generators holding it move to their next
+// cached row (looking up RC more when the cache runs out), and the search
+// goes on.  Nothing is sorted or merged.  Only apparent owners are added
+// here (this runs before any column of the dimension is finalized); a
+// pivot owned by a finished column ends the call with ST_BUDGET.  On
+// completion with additions the generators are stored (store_generators).
+constexpr int RGEN = 16;
 template <int P>
-__device__ void reduce_one(const Ctx& c, int64_t j, int budget, uint64_t* stage, uint64_t* bufA, uint64_t* bufB,
-                           int64_t cap, uint64_t& out_key, uint8_t& out_status, uint32_t& out_adds) {
+__device__ void reduce_one(const Ctx& c, int64_t j, int budget, uint64_t* stage, uint64_t& out_key,
+                           uint8_t& out_status, uint32_t& out_adds) {
+    static_assert(RGEN * (RC + 1 + sizeof(Simplex<P>) / 8 + 1) <= STAGE, "generators fit the stage");
     const int lane = threadIdx.x & 31;
     const uint64_t self_key = c.cols[j];
     Simplex<P> s, o;
     int64_t opos = -1;
     load_col<P>(c, self_key, s);
-    uint64_t piv = warp_column_pivot<P>(c, s);
+    uint64_t* gc = stage;                                                      // [RGEN][RC] cached rows
+    int* gh = reinterpret_cast<int*>(stage + RGEN * RC);                       // [RGEN] position in the cache
+    Simplex<P>* gs = reinterpret_cast<Simplex<P>*>(stage + RGEN * (RC + 1));  // [RGEN] generators
+    uint64_t rows[RC];
+    warp_rows_above<P, 1>(c, s, false, 0, rows);  // the pivot of D_j; more rows only if it is added to
+    uint64_t piv = rows[0];
     out_adds = 0;
     if (lane == 0) c.rc_len[j] = 0;
     if (piv == EMPTY) { out_key = EMPTY; out_status = ST_COMPLETE; return; }
     if (!warp_owner<P>(c, piv, self_key, o, opos)) { out_key = piv; out_status = ST_COMPLETE; return; }
     if (budget <= 0) { out_key = piv; out_status = ST_BUDGET; return; }  // the pivot has an owner: not settled here
-    uint64_t* W = bufA;
-    uint64_t* spare = bufB;
-    int64_t a = warp_add_coboundary<P>(c, s, stage, W, spare, 0, cap);
-    if (a < 0) { out_key = piv; out_status = ST_OVERFLOW; return; }
+    // a generator enters with its smallest row as the last cached one: when
+    // that row cancels, the next RC are looked up
+    if (lane == 0) {
+        gs[0] = s;
+        gh[0] = RC - 1;
+        gc[RC - 1] = piv;
+    }
+    __syncwarp();
+    int m = 1;
     uint32_t adds = 0;
+    auto current = [&](int i) -> uint64_t { const int h = gh[i]; return h < RC ? gc[i * RC + h] : EMPTY; };
     for (;;) {
-        if ((int)adds >= budget) { out_key = piv; out_status = ST_BUDGET; out_adds = adds; return; }
-        const int64_t na = warp_add_owner<P>(c, o, opos, stage, W, spare, a, cap);
-        if (na < 0) { out_key = piv; out_status = ST_OVERFLOW; out_adds = adds; return; }
+        if ((int)adds >= budget || m >= RGEN || opos >= 0) {
+            out_key = piv; out_status = ST_BUDGET; out_adds = adds;
+            return;
+        }
+        // W <- W + D_o: its smallest row is piv (o owns it)
+        if (lane == 0) {
+            gs[m] = o;
+            gh[m] = RC - 1;
+            gc[m * RC + RC - 1] = piv;
+        }
+        __syncwarp();
+        ++m;
         ++adds;
-        a = na;
-        if (a == 0) { out_key = EMPTY; out_status = ST_COMPLETE; out_adds = adds; return; }
-        piv = W[0];
+        for (;;) {
+            uint64_t cm = EMPTY;
+            int cnt = 0;
+            for (int i = 0; i < m; ++i) {
+                const uint64_t x = current(i);
+                if (x < cm) { cm = x; cnt = 1; } else if (x == cm) ++cnt;
+            }
+            if (cm == EMPTY || (cnt & 1)) { piv = cm; break; }
+            for (int i = 0; i < m; ++i) {  // cm cancels: the generators holding it move on
+                if (current(i) != cm) continue;
+                const int h = gh[i] + 1;
+                const uint64_t last = gc[i * RC + RC - 1];
+                __syncwarp();
+                if (h < RC || last == EMPTY) {  // the next cached row, or none left
+                    if (lane == 0) gh[i] = h < RC ? h : RC;
+                } else {
+                    const Simplex<P> g = gs[i];
+                    warp_rows_above<P>(c, g, true, last, rows);
+                    if (lane == 0) {
+                        gh[i] = 0;
+#pragma unroll
+                        for (int r = 0; r < RC; ++r) gc[i * RC + r] = rows[r];
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (piv == EMPTY) { out_key = EMPTY; out_status = ST_COMPLETE; out_adds = adds; return; }
         if (!warp_owner<P>(c, piv, self_key, o, opos)) {
             out_key = piv;
             out_status = ST_COMPLETE;
             out_adds = adds;
-            store_reduced(c, j, W, a);
+            store_generators<P>(c, j, gs, m);
             return;
         }
     }
@@ -1128,19 +1109,6 @@ __device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, in
     return heavy_add_coboundary<P>(c, S, B, bcap, x, c.R.n - 1);
 }
 
-// W <- W + R_o where R_o is a stored reduced column (sorted, unique).
-__device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, int64_t opos) {
-    const uint64_t* run = c.pool + c.rc_off[opos];
-    const int64_t len = c.rc_len[opos];
-    for (int64_t base = 0; base < len; base += HSTAGE) {
-        const int cnt = (int)min((int64_t)HSTAGE, len - base);
-        for (int i = threadIdx.x; i < cnt; i += HT) S.stage[i] = run[base + i];
-        __syncthreads();
-        if (!heavy_add_run(S, B, bcap, cnt)) return false;
-    }
-    return true;
-}
-
 // Sort stage[0..cnt) (cnt <= HSTAGE), keep one row of every run of odd
 // length (Z/2) and add the result to W.
 __device__ bool heavy_flush_stage(HeavySmem& S, uint64_t* B, int64_t bcap, int cnt) {
@@ -1168,6 +1136,43 @@ __device__ bool heavy_flush_stage(HeavySmem& S, uint64_t* B, int64_t bcap, int c
     if (keep1) S.stage[tot0 + pos1] = v1;
     __syncthreads();
     return heavy_add_run(S, B, bcap, tot0 + tot1);
+}
+
+// W <- W + R_o where R_o is stored as its generators (store_generators):
+// their coboundaries' rows are generated in turn, the rows at or above the
+// split go straight to the back and the rest collect in the stage, which is
+// flushed (sorted, cancelled, merged) only when the next pass might not fit
+// -- one merge for several coboundaries instead of one addition each.
+template <int P>
+__device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, int64_t opos) {
+    const uint64_t* gk = c.pool + c.rc_off[opos];
+    const int64_t len = c.rc_len[opos];
+    int sc = 0;  // rows in the stage
+    for (int64_t i = 0; i < len; ++i) {
+        Simplex<P> g;
+        load_col<P>(c, gk[i], g);
+        for (int64_t base = c.R.n - 1; base >= 0; base -= HT) {
+            uint64_t key = EMPTY;
+            const bool ok = cob_row<P>(c, g, base - (int64_t)threadIdx.x, key);
+            const bool lt = ok && key < S.Ks, ge = ok && !lt;
+            int tot;
+            const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
+            const int nlt = tot & 0xFFFF, nge = tot >> 16;
+            if (sc + nlt > HSTAGE) {  // flushing may lower Ks: rows kept below the old split stay valid
+                if (!heavy_flush_stage(S, B, bcap, sc)) return false;
+                sc = 0;
+            }
+            const int64_t bs = S.bsize;
+            if (bs + nge > bcap) return false;
+            if (ge) B[bs + (packed >> 16)] = key;
+            if (lt) S.stage[sc + (packed & 0xFFFF)] = key;
+            sc += nlt;
+            __syncthreads();
+            if (threadIdx.x == 0) S.bsize = bs + nge;
+            __syncthreads();
+        }
+    }
+    return sc == 0 || heavy_flush_stage(S, B, bcap, sc);
 }
 
 // W <- W + R_o where R_o = rows[0..len) is any multiset of rows (for example
