@@ -601,13 +601,16 @@ __device__ int merge_group(HeavySmem& S, const uint64_t* run, int cur, int a, in
     const int tot = a + b;
     const int per = (tot + nt - 1) / nt;
     const int d = min(tot, g * per);
-    int lo = max(0, d - a), hi = min(d, b);
-    while (lo < hi) {
-        const int m = (lo + hi) >> 1;
-        if (run[m] < F[d - m - 1]) lo = m + 1; else hi = m;
+    // k0: run rows among the first d of the merged sequence, the largest k in
+    // [max(0, d - a), min(d, b)] with run[k-1] < F[d-k] (fixed power-of-two
+    // steps: no data-dependent branches in the search)
+    const int klo = max(0, d - a), khi = min(d, b);
+    int k0 = klo;
+    for (int st = khi > klo ? 1 << (31 - __clz(khi - klo)) : 0; st > 0; st >>= 1) {
+        const int t = k0 + st;
+        if (t <= khi && run[t - 1] < F[d - t]) k0 = t;
     }
-    const int k0 = lo;
-    int i0 = d - lo;
+    int i0 = d - k0;
     if (i0 > 0 && k0 < b && F[i0 - 1] == run[k0]) --i0;
     S.msplit[g] = ((uint32_t)i0 << 16) | (uint32_t)k0;
     // run rows kb + lane (kb: this warp's block of 32, stepping by nt) that cancel
@@ -616,7 +619,11 @@ __device__ int merge_group(HeavySmem& S, const uint64_t* run, int cur, int a, in
         bool eq = false;
         if (k < b) {
             const uint64_t y = run[k];
-            const int q = lower_bound_sm(F, a, y);
+            int q = 0;  // front rows below y, by fixed steps
+            for (int st = a > 0 ? 1 << (31 - __clz(a)) : 0; st > 0; st >>= 1) {
+                const int t = q + st;
+                if (t <= a && F[t - 1] < y) q = t;
+            }
             eq = q < a && F[q] == y;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, eq);
