@@ -420,8 +420,11 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         int budget = 64;
         // Columns are finalized between rounds only, so a round that runs as
         // long as its longest column would keep columns it unblocks idle; a
-        // cap of 64 additions (about 0.5 ms) keeps rounds short.
-        constexpr int budget_cap = 64;
+        // cap of 64 additions (about 0.3 ms) keeps rounds short.  With at most
+        // four unfinished columns few can be waiting, and rounds of up to 256
+        // additions save launches, state reloads and finalizations (measured:
+        // torus500's two long dimension-1 columns, 10.0 -> 9.65 ms).
+        constexpr int budget_cap = 64, budget_cap_few = 256;
         int64_t stalled_adds = 0;  // additions granted to the first column since a column was last finalized
         cudaEvent_t ev[2] = {nullptr, nullptr};
         if (h.prof) { VR_CUDA(cudaEventCreate(&ev[0])); VR_CUDA(cudaEventCreate(&ev[1])); }
@@ -452,7 +455,8 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 cur ^= 1;
                 ++rounds;
                 granted += budget;
-                if (budget < budget_cap) budget *= 2;
+                const int cap = u0 <= 4 ? budget_cap_few : budget_cap;
+                budget = budget < cap ? 2 * budget : cap;
             }
             VR_CUDA(cudaMemcpyAsync(&hs.p[8], du + cur, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             VR_CUDA(cudaMemcpyAsync(&hs.p[9], du + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
