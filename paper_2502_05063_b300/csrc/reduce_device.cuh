@@ -1035,33 +1035,21 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
         uint64_t pn = EMPTY;
         bool certain = false;
         if (wid == 0) {
-            // bitonic merge of the two 32-row heads in registers: lane L holds
-            // positions L (front head) and 32 + L (run head, reversed)
-            uint64_t e0 = lane < a ? F[lane] : EMPTY, e1 = (31 - lane) < nlt ? run[31 - lane] : EMPTY;
-            {
-                const uint64_t lo = e0 < e1 ? e0 : e1, hi = e0 < e1 ? e1 : e0;
-                e0 = lo;
-                e1 = hi;
-            }
+            // the smallest row of F XOR run among the two 32-row heads: a row
+            // survives unless the other head holds it (both arrays are unique),
+            // exact for rows below row 32 of both
+            const int fa = min(a, 32), fr = min(nlt, 32);
+            const uint64_t f = lane < a ? F[lane] : EMPTY, r = lane < nlt ? run[lane] : EMPTY;
+            int qf = 0, qr = 0;  // rows of the other head below f / r, by fixed steps
 #pragma unroll
-            for (int j = 16; j > 0; j >>= 1) {
-                const uint64_t o0 = __shfl_xor_sync(0xffffffffu, e0, j), o1 = __shfl_xor_sync(0xffffffffu, e1, j);
-                const bool low = (lane & j) == 0;
-                e0 = low ? (e0 < o0 ? e0 : o0) : (e0 < o0 ? o0 : e0);
-                e1 = low ? (e1 < o1 ? e1 : o1) : (e1 < o1 ? o1 : e1);
+            for (int st = 16; st > 0; st >>= 1) {
+                if (qf + st <= fr && run[qf + st - 1] < f) qf += st;
+                if (qr + st <= fa && F[qr + st - 1] < r) qr += st;
             }
-            // equal rows are adjacent pairs (each array is unique); a row survives
-            // unless a neighbour equals it
-            const uint64_t p0 = __shfl_up_sync(0xffffffffu, e0, 1), n0 = __shfl_down_sync(0xffffffffu, e0, 1);
-            const uint64_t p1 = __shfl_up_sync(0xffffffffu, e1, 1), n1 = __shfl_down_sync(0xffffffffu, e1, 1);
-            const uint64_t last0 = __shfl_sync(0xffffffffu, e0, 31), first1 = __shfl_sync(0xffffffffu, e1, 0);
-            const uint64_t prev0 = lane == 0 ? EMPTY - 1 : p0, next0 = lane == 31 ? first1 : n0;
-            const uint64_t prev1 = lane == 0 ? last0 : p1, next1 = lane == 31 ? EMPTY - 1 : n1;
-            const bool s0 = e0 != EMPTY && e0 != prev0 && e0 != next0;
-            const bool s1 = e1 != EMPTY && e1 != prev1 && e1 != next1;
-            const uint32_t b0 = __ballot_sync(0xffffffffu, s0), b1 = __ballot_sync(0xffffffffu, s1);
-            pn = b0 ? __shfl_sync(0xffffffffu, e0, __ffs(b0) - 1)
-                    : (b1 ? __shfl_sync(0xffffffffu, e1, __ffs(b1) - 1) : EMPTY);
+            const bool fs = f != EMPTY && !(qf < fr && run[qf] == f);
+            const bool rs = r != EMPTY && !(qr < fa && F[qr] == r);
+            const uint64_t mine = fs ? (rs && r < f ? r : f) : (rs ? r : EMPTY);
+            pn = warp_min_u64(mine);
             const uint64_t f32 = a > 32 ? F[32] : EMPTY, r32 = nlt > 32 ? run[32] : EMPTY;
             certain = pn < (f32 < r32 ? f32 : r32);
             if (lane == 0) { S.sel = certain ? pn : EMPTY; }
