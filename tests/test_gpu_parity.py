@@ -89,6 +89,24 @@ def test_radix_sort_matches_numpy(vr, num, bits):
     assert vd.cpu().numpy().view(np.uint64).tolist() == vals[order].tolist()
 
 
+@pytest.mark.parametrize("num,bits", [(300, 20), (4096, 36), (9000, 40), (40000, 28)])
+def test_radix_sort_ignores_bits_above(vr, num, bits):
+    """Only the low `bits` bits order the keys (stably); the keys keep their high bits."""
+    import torch
+    rng = np.random.default_rng(7 * num + bits)
+    keys = rng.integers(0, 2 ** 63, size=num, dtype=np.int64).astype(np.uint64)
+    low = keys & np.uint64((1 << bits) - 1)
+    low[: num // 4] = low[num // 4: 2 * (num // 4)]  # equal low parts, different high parts
+    keys = (keys & ~np.uint64((1 << bits) - 1)) | low
+    vals = np.arange(num, dtype=np.uint64)
+    kd = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    vd = torch.from_numpy(vals.view(np.int64).copy()).cuda()
+    vr.sort_u64(kd, vd, bits)
+    order = np.argsort(low, kind="stable")
+    assert kd.cpu().numpy().view(np.uint64).tolist() == keys[order].tolist()
+    assert vd.cpu().numpy().view(np.uint64).tolist() == vals[order].tolist()
+
+
 # --------------------------------------------------------------------------
 # barcodes: random small clouds, all dimensions, exact
 # --------------------------------------------------------------------------
