@@ -6,7 +6,9 @@
 // unsigned integer, and only the significant low bits are sorted.
 //
 // Up to 4096 keys: one block, a bitonic network on (key, index) pairs in
-// shared memory (k_small_sort), the same stable order in one launch.
+// shared memory (k_small_sort), the same stable order in one launch; up to
+// 32768: chunks of 4096 so sorted, then each key placed by searching the
+// other chunks (two launches).
 // Otherwise one pass per 8-bit digit, three kernels per pass, no inter-block waits:
 //   1. k_hist    per-tile digit histogram, stored digit-major
 //   2. k_scan    exclusive scan of the (digit, tile) counts in one block
@@ -189,6 +191,74 @@ k_small_sort(K* __restrict__ keys, V* __restrict__ vals, int num, int len, K mas
     }
 }
 
+// Up to CHUNKED_MAX keys: chunks of SMALL_MAX are sorted by one block each
+// (same order as k_small_sort: masked key, then input index), then every key
+// finds its place by searching the other chunks -- two launches.
+constexpr int CHUNKED_MAX = 8 * SMALL_MAX;
+
+template <class K>
+__global__ void __launch_bounds__(SMALL_THREADS)
+k_chunk_sort(const K* __restrict__ keys, int num, K mask, K* __restrict__ ck, uint32_t* __restrict__ ci) {
+    __shared__ K a[SMALL_MAX];
+    __shared__ uint32_t ix[SMALL_MAX];
+    const int base = blockIdx.x * SMALL_MAX;
+    const int cnt = min(SMALL_MAX, num - base);
+    for (int i = threadIdx.x; i < SMALL_MAX; i += SMALL_THREADS) {
+        a[i] = i < cnt ? (keys[base + i] & mask) : ~(K)0;
+        ix[i] = (uint32_t)(base + i);  // padding: indices past num, sorted last
+    }
+    __syncthreads();
+    constexpr int half = SMALL_MAX >> 1;
+    for (int k = 2; k <= SMALL_MAX; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < half; p += SMALL_THREADS) {
+                const int i = 2 * p - (p & (j - 1));
+                const K x = a[i], y = a[i + j];
+                const uint32_t xi = ix[i], yi = ix[i + j];
+                const bool gt = x > y || (x == y && xi > yi);
+                if (gt == ((i & k) == 0)) {
+                    a[i] = y; a[i + j] = x;
+                    ix[i] = yi; ix[i + j] = xi;
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < cnt; i += SMALL_THREADS) {
+        ck[base + i] = a[i];
+        ci[base + i] = ix[i];
+    }
+}
+
+// Key t of chunk c (rank r in it) goes to r plus the keys of the other chunks
+// before it in (masked key, index) order.
+template <class K, class V, bool HAS_V>
+__global__ void k_chunk_place(const K* __restrict__ keys, const V* __restrict__ vals, int num,
+                              const K* __restrict__ ck, const uint32_t* __restrict__ ci, K* __restrict__ kout,
+                              V* __restrict__ vout) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= num) return;
+    const int c = t / SMALL_MAX, r = t % SMALL_MAX;
+    const K x = ck[t];
+    const uint32_t xi = ci[t];
+    const int nch = (num + SMALL_MAX - 1) / SMALL_MAX;
+    int pos = r;
+    for (int c2 = 0; c2 < nch; ++c2) {
+        if (c2 == c) continue;
+        const int b = c2 * SMALL_MAX, n2 = min(SMALL_MAX, num - b);
+        int q = 0;  // keys of chunk c2 before (x, xi), by fixed steps
+        for (int st = 1 << (31 - __clz(n2)); st > 0; st >>= 1) {
+            const int u = q + st;
+            if (u <= n2) {
+                const K y = ck[b + u - 1];
+                if (y < x || (y == x && ci[b + u - 1] < xi)) q = u;
+            }
+        }
+        pos += q;
+    }
+    kout[pos] = keys[xi];
+    if (HAS_V) vout[pos] = vals[xi];
+}
+
 template <class K, class V, bool HAS_V>
 void radix_sort_impl(Workspace& ws, K* keys, V* vals, int64_t num, int bits) {
     if (num <= 1 || bits <= 0) return;
@@ -202,6 +272,21 @@ void radix_sort_impl(Workspace& ws, K* keys, V* vals, int64_t num, int bits) {
                                      (int)(SMALL_MAX * (sizeof(K) + sizeof(uint32_t)))));
         k_small_sort<K, V, HAS_V><<<1, SMALL_THREADS, smem, ws.stream>>>(keys, vals, (int)num, len, mask);
         VR_CUDA(cudaGetLastError());
+        return;
+    }
+    if (num <= CHUNKED_MAX) {
+        const K mask = bits >= (int)(8 * sizeof(K)) ? ~(K)0 : (K)((((K)1) << bits) - 1);
+        const int nch = (int)((num + SMALL_MAX - 1) / SMALL_MAX);
+        K* ck = ws.alloc_n<K>(num);
+        uint32_t* ci = ws.alloc_n<uint32_t>(num);
+        K* kout = ws.alloc_n<K>(num);
+        V* vout = HAS_V ? ws.alloc_n<V>(num) : nullptr;
+        k_chunk_sort<K><<<nch, SMALL_THREADS, 0, ws.stream>>>(keys, (int)num, mask, ck, ci);
+        k_chunk_place<K, V, HAS_V><<<(unsigned)((num + 255) / 256), 256, 0, ws.stream>>>(keys, vals, (int)num, ck, ci,
+                                                                                          kout, vout);
+        VR_CUDA(cudaGetLastError());
+        VR_CUDA(cudaMemcpyAsync(keys, kout, num * sizeof(K), cudaMemcpyDeviceToDevice, ws.stream));
+        if (HAS_V) VR_CUDA(cudaMemcpyAsync(vals, vout, num * sizeof(V), cudaMemcpyDeviceToDevice, ws.stream));
         return;
     }
     const int64_t tiles = (num + RS_TILE - 1) / RS_TILE;

@@ -89,7 +89,7 @@ def test_radix_sort_matches_numpy(vr, num, bits):
     assert vd.cpu().numpy().view(np.uint64).tolist() == vals[order].tolist()
 
 
-@pytest.mark.parametrize("num,bits", [(300, 20), (4096, 36), (9000, 40), (40000, 28)])
+@pytest.mark.parametrize("num,bits", [(300, 20), (4096, 36), (9000, 40), (4097, 64), (32768, 30), (40000, 28)])
 def test_radix_sort_ignores_bits_above(vr, num, bits):
     """Only the low `bits` bits order the keys (stably); the keys keep their high bits."""
     import torch
