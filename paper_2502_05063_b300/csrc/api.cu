@@ -30,6 +30,7 @@ static thread_local char g_err[512];
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
     snprintf(g_err, sizeof g_err, "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+    if (log_enabled()) fprintf(stderr, "[vr] CUDA error: %s\n", g_err);
 }
 
 static void configure_pool_once() {

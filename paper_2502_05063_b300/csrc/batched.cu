@@ -618,7 +618,8 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
             emit_block(A, M, 1, cloud, h1tmp, h, R, B);
         }
         VR_PHASE(7);
-        if (A.prof && threadIdx.x == 0) A.prof[16 + cloud] = (unsigned long long)(clock64() - t_cloud);
+        if (A.prof && threadIdx.x == 0 && cloud >= 0 && cloud < A.num)
+            A.prof[16 + cloud] = (unsigned long long)(clock64() - t_cloud);
     }
 #undef VR_PHASE
 }
@@ -628,10 +629,13 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
 __global__ void k_batch_gather(const PairRec* __restrict__ recs, const int32_t* __restrict__ edges,
                                const int64_t* __restrict__ start, const int32_t* __restrict__ count,
                                const int64_t* __restrict__ off, const int64_t* __restrict__ poffs, int num,
-                               vr_pair* __restrict__ out, int32_t* __restrict__ out_edges) {
+                               int64_t cap, vr_pair* __restrict__ out, int32_t* __restrict__ out_edges) {
     for (int cl = blockIdx.x; cl < num; cl += gridDim.x) {
         const int64_t s = start[cl], o = off[cl];
         const int cnt = count[cl];
+        // past the planned room (the host then grows the buffers and reruns):
+        // neither the records nor the output hold these pairs
+        if (cnt <= 0 || s < 0 || s + cnt > cap || o + cnt > cap) continue;
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             const PairRec r = recs[s + i];
             vr_pair v;
@@ -728,11 +732,14 @@ void record_launches(BatchPlan& P, cudaStream_t s) {
     BatchArgs& A = P.args;
     VR_CUDA(cudaMemsetAsync(A.work, 0, 8 * sizeof(unsigned long long), s));  // work, used[2], stats[4]
     VR_CUDA(cudaMemsetAsync(A.cloud_err, 0, P.num * sizeof(int32_t), s));
+    // a cloud recomputed by the host (cloud_err) emits no pairs of some dimension:
+    // its count must read 0, not what a previous launch or the allocation left
+    for (int p = 0; p <= P.dmax; ++p) VR_CUDA(cudaMemsetAsync(A.count[p], 0, P.num * sizeof(int32_t), s));
     k_batched<<<P.slots, HT, sizeof(BatchSmem), s>>>(A);
     for (int p = 0; p <= P.dmax; ++p) {
         k_exclusive_scan_i64<<<1, 1024, 0, s>>>(A.count[p], P.num, P.off[p]);
         k_batch_gather<<<std::min(P.num, 4096), 128, 0, s>>>(A.recs[p], A.edges[p], A.start[p], A.count[p], P.off[p],
-                                                             P.offs, P.num, P.pairs[p],
+                                                             P.offs, P.num, A.cap[p], P.pairs[p],
                                                              P.want_edges ? P.edges[p] : nullptr);
     }
     VR_CUDA(cudaGetLastError());
