@@ -95,3 +95,23 @@ def test_batched_repeat_and_shapes(vr):
     with pytest.raises(vr.VRError):
         big = np.zeros((300, 3), np.float32)
         vr.barcodes_batched(big, np.array([0, 300]), dmax=1)
+
+
+def test_batched_output_larger_than_planned(vr):
+    """More H1 pairs than the first call's estimate for the shape (64 per cloud
+    plus 1024): the host grows the output buffers and reruns, and no pair lands
+    outside them meanwhile.  Every fourth cloud equals the single-cloud path,
+    and the pair counts of all clouds match it."""
+    rng = np.random.default_rng(77)
+    clouds = [rng.random((256, 3)).astype(np.float32) for _ in range(64)]
+    clouds[5] = clouds[5][:255]  # a total no other test uses: a fresh plan
+    pts, offs = synth.pack(clouds)
+    bb = vr.barcodes_batched(pts, offs, dmax=1)
+    counts = [len(rows(bb.cloud(i, 1))) for i in range(len(clouds))]
+    assert sum(counts) > 64 * len(clouds) + 1024  # the case this test is for
+    for i in range(len(clouds)):
+        single = vr.barcodes(points=clouds[i], dmax=1)
+        assert counts[i] == len(single.pairs[1]), i
+        if i % 4 == 0:
+            for p in range(2):
+                assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
