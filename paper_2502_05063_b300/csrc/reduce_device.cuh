@@ -436,6 +436,7 @@ constexpr int FKEEP = FC - 1024; // front size kept after a spill
 constexpr int HSTAGE = 1024;     // rows generated or copied per pass (power of two >= HT)
 constexpr int REFILL = FC / 2;   // rows promoted from the back per refill (at most)
 static_assert(HSTAGE == 2 * HT, "a flushed stage holds two rows per thread");
+static_assert(FKEEP + HSTAGE <= FC, "a merge writes a front of FKEEP rows and a run of HSTAGE into FC");
 static_assert(HW <= 32, "block scans keep one total per warp in one warp");
 static_assert(FC < (1 << 16) && HSTAGE < (1 << 16), "merge splits pack two 16-bit indices");
 
@@ -730,8 +731,10 @@ __device__ void heavy_compact_back(HeavySmem& S, uint64_t* B) {
 }
 
 // Refill an empty front from B.  Returns false if the column is zero.
+// A refilled front holds at most FKEEP rows, like a spilled one: every merge
+// writes the front and a run of up to HSTAGE rows into a buffer of FC.
 // Two splits Ta < Tb come from a sorted sample of B (its quantiles for
-// about 0.45 FC and 0.83 FC rows).  One pass over B collects the positions
+// about 0.5 FKEEP and 0.9 FKEEP rows).  One pass over B collects the positions
 // of the rows below Tb (room for 2 FC); if they fit the front they are
 // taken, else, if the rows below Ta among them do, those are -- so a
 // refill takes close to a full front without a second pass over B (a pass
@@ -763,8 +766,8 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
             for (int i = threadIdx.x; i < NS; i += HT) Sm[i] = B[(int64_t)i * stride];
             __syncthreads();
             block_bitonic(Sm, NS);
-            qa = (int)((double)FC * 0.45 * NS / (double)bsz);
-            qb = (int)((double)FC * 0.83 * NS / (double)bsz);
+            qa = (int)((double)FKEEP * 0.5 * NS / (double)bsz);
+            qb = (int)((double)FKEEP * 0.9 * NS / (double)bsz);
             qa = qa < 1 ? 1 : (qa > NS - 2 ? NS - 2 : qa);
             qb = qb <= qa ? qa + 1 : (qb > NS - 1 ? NS - 1 : qb);
             Ta = Sm[qa];
@@ -806,17 +809,17 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
             __syncthreads();
             cnt = cnt_sh;
             __syncthreads();
-            if (cnt >= 1 && cnt <= FC) { T = Tb; nsel = cnt; break; }
+            if (cnt >= 1 && cnt <= FKEEP) { T = Tb; nsel = cnt; break; }
             int ca = -1;  // rows below Ta, when known
-            if (cnt > FC && cnt <= 2 * FC && Ta < Tb) {
+            if (cnt > FKEEP && cnt <= 2 * FC && Ta < Tb) {
                 int c = 0;
                 for (int i = threadIdx.x; i < cnt; i += HT) c += B[P[i]] < Ta;
                 int tot;
                 block_excl_scan(c, S.ws, &tot);
                 ca = tot;
-                if (ca >= 1 && ca <= FC) { T = Ta; nsel = ca; filtered = true; break; }
+                if (ca >= 1 && ca <= FKEEP) { T = Ta; nsel = ca; filtered = true; break; }
             }
-            if (cnt > FC && have_min && Tb == bmin + 1) { T = Tb; nsel = cnt; break; }  // one key, more copies than fit
+            if (cnt > FKEEP && have_min && Tb == bmin + 1) { T = Tb; nsel = cnt; break; }  // one key, more copies than fit
             if (!have_min) {
                 if (threadIdx.x == 0) min_sh = EMPTY;
                 __syncthreads();
@@ -856,7 +859,7 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
             }
         }
         HPROF_LAP(5);
-        if (nsel > FC) {  // every copy of bmin becomes a hole; its parity decides
+        if (nsel > FKEEP) {  // every copy of bmin becomes a hole; its parity decides
             for (int64_t i = threadIdx.x; i < bsz; i += HT)
                 if (B[i] == bmin) B[i] = EMPTY;
             __syncthreads();
