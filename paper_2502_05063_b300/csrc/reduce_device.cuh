@@ -434,9 +434,10 @@ constexpr int HW = HT / 32;
 constexpr int FC = 4096;         // front capacity
 constexpr int FKEEP = FC - 1024; // front size kept after a spill
 constexpr int HSTAGE = 1024;     // rows generated or copied per pass (power of two >= HT)
-constexpr int REFILL = FC / 2;   // rows promoted from the back per refill (at most)
 static_assert(HSTAGE == 2 * HT, "a flushed stage holds two rows per thread");
 static_assert(FKEEP + HSTAGE <= FC, "a merge writes a front of FKEEP rows and a run of HSTAGE into FC");
+constexpr int REFILL_MAX = FC - HT;  // rows a refill may leave in the front
+static_assert(REFILL_MAX + HT <= FC, "a pass of generated rows (at most HT) fits after a refill");
 static_assert(HW <= 32, "block scans keep one total per warp in one warp");
 static_assert(FC < (1 << 16) && HSTAGE < (1 << 16), "merge splits pack two 16-bit indices");
 
@@ -668,6 +669,24 @@ __device__ bool heavy_spill(HeavySmem& S, uint64_t* B, int64_t bcap, int na) {
 // entirely below Ks; the whole block merges, see merge_group).
 __device__ bool heavy_merge_front(HeavySmem& S, uint64_t* B, int64_t bcap, const uint64_t* run, int b) {
     if (b == 0) return true;
+    if (S.fsize + b > FC) {
+        // a run of more than HT rows into a refilled front (up to REFILL_MAX
+        // rows): the front's top rows go to B first and the split drops to the
+        // first of them; the run rows at or above it follow them
+        const int keep = FC - b;
+        const uint64_t* F0 = S.buf[S.cur];
+        const uint64_t nks = F0[keep];
+        if (!heavy_append(S, B, bcap, F0 + keep, S.fsize - keep)) return false;
+        const int lo = lower_bound_sm(run, b, nks);
+        if (!heavy_append(S, B, bcap, run + lo, b - lo)) return false;
+        if (threadIdx.x == 0) {
+            S.Ks = nks;
+            S.fsize = keep;
+        }
+        __syncthreads();
+        b = lo;
+        if (b == 0) return true;
+    }
     const int cur = S.cur, a = S.fsize;
     HPROF_T0();
     const int na = merge_group(S, run, cur, a, b, 0, HT, 0);
@@ -731,12 +750,13 @@ __device__ void heavy_compact_back(HeavySmem& S, uint64_t* B) {
 }
 
 // Refill an empty front from B.  Returns false if the column is zero.
-// A refilled front holds at most FKEEP rows, like a spilled one: every merge
-// writes the front and a run of up to HSTAGE rows into a buffer of FC.
-// Two splits Ta < Tb come from a sorted sample of B (its quantiles for
-// about 0.5 FKEEP and 0.9 FKEEP rows).  One pass over B collects the positions
-// of the rows below Tb (room for 2 FC); if they fit the front they are
-// taken, else, if the rows below Ta among them do, those are -- so a
+// A refilled front holds at most REFILL_MAX = FC - HT rows: a pass of
+// generated rows (at most HT) still fits beside it, and heavy_merge_front
+// spills before a longer run.  Two splits Ta < Tb come from a sorted sample
+// of B (its quantiles for about 0.5 and 0.9 REFILL_MAX rows).  One pass
+// over B collects the positions of the rows below Tb (room for 2 FC); if
+// they fit the front they are taken, else, if the rows below Ta among them
+// do, those are -- so a
 // refill takes close to a full front without a second pass over B (a pass
 // costs the same for either, and fewer, larger refills are cheaper).  If
 // neither fits, the splits move and the pass repeats.  The rows are
@@ -766,8 +786,8 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
             for (int i = threadIdx.x; i < NS; i += HT) Sm[i] = B[(int64_t)i * stride];
             __syncthreads();
             block_bitonic(Sm, NS);
-            qa = (int)((double)FKEEP * 0.5 * NS / (double)bsz);
-            qb = (int)((double)FKEEP * 0.9 * NS / (double)bsz);
+            qa = (int)((double)REFILL_MAX * 0.5 * NS / (double)bsz);
+            qb = (int)((double)REFILL_MAX * 0.9 * NS / (double)bsz);
             qa = qa < 1 ? 1 : (qa > NS - 2 ? NS - 2 : qa);
             qb = qb <= qa ? qa + 1 : (qb > NS - 1 ? NS - 1 : qb);
             Ta = Sm[qa];
@@ -809,17 +829,17 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
             __syncthreads();
             cnt = cnt_sh;
             __syncthreads();
-            if (cnt >= 1 && cnt <= FKEEP) { T = Tb; nsel = cnt; break; }
+            if (cnt >= 1 && cnt <= REFILL_MAX) { T = Tb; nsel = cnt; break; }
             int ca = -1;  // rows below Ta, when known
-            if (cnt > FKEEP && cnt <= 2 * FC && Ta < Tb) {
+            if (cnt > REFILL_MAX && cnt <= 2 * FC && Ta < Tb) {
                 int c = 0;
                 for (int i = threadIdx.x; i < cnt; i += HT) c += B[P[i]] < Ta;
                 int tot;
                 block_excl_scan(c, S.ws, &tot);
                 ca = tot;
-                if (ca >= 1 && ca <= FKEEP) { T = Ta; nsel = ca; filtered = true; break; }
+                if (ca >= 1 && ca <= REFILL_MAX) { T = Ta; nsel = ca; filtered = true; break; }
             }
-            if (cnt > FKEEP && have_min && Tb == bmin + 1) { T = Tb; nsel = cnt; break; }  // one key, more copies than fit
+            if (cnt > REFILL_MAX && have_min && Tb == bmin + 1) { T = Tb; nsel = cnt; break; }  // one key, more copies than fit
             if (!have_min) {
                 if (threadIdx.x == 0) min_sh = EMPTY;
                 __syncthreads();
@@ -859,7 +879,7 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
             }
         }
         HPROF_LAP(5);
-        if (nsel > FKEEP) {  // every copy of bmin becomes a hole; its parity decides
+        if (nsel > REFILL_MAX) {  // every copy of bmin becomes a hole; its parity decides
             for (int64_t i = threadIdx.x; i < bsz; i += HT)
                 if (B[i] == bmin) B[i] = EMPTY;
             __syncthreads();
