@@ -101,15 +101,6 @@ __device__ void warp_bitonic(uint64_t* stage, int len) {
         }
 }
 
-__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t len, uint64_t x) {
-    int64_t lo = 0, hi = len;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
     const uint32_t hi = __reduce_min_sync(0xffffffffu, (uint32_t)(x >> 32));
     const uint32_t lo = __reduce_min_sync(0xffffffffu, (uint32_t)(x >> 32) == hi ? (uint32_t)x : 0xffffffffu);
@@ -125,13 +116,12 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
 constexpr int RC = 4;
 template <int P, int K = RC>
 __device__ void warp_rows_above(const Ctx& c, const Simplex<P>& x, bool has_cut, uint64_t cut, uint64_t* out) {
-    constexpr int RC = K;
     const int lane = threadIdx.x & 31;
     const int64_t n = c.R.n;
     const uint32_t rcut = has_cut ? (uint32_t)(cut >> c.rcb) : 0u;
-    uint64_t t[RC];
+    uint64_t t[K];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) t[r] = EMPTY;
+    for (int r = 0; r < K; ++r) t[r] = EMPTY;
     for (int64_t base = n - 1; base >= 0; base -= 32) {
         const int64_t w = base - lane;
         bool ok = w >= 0;
@@ -141,12 +131,12 @@ __device__ void warp_rows_above(const Ctx& c, const Simplex<P>& x, bool has_cut,
             uint32_t rt = x.r;
 #pragma unroll
             for (int q = 0; q <= P; ++q) rt = max(rt, c.R(x.v[q], w));
-            if (rt <= c.thr && rt >= rcut && ((uint64_t)rt << c.rcb) <= t[RC - 1]) {
+            if (rt <= c.thr && rt >= rcut && ((uint64_t)rt << c.rcb) <= t[K - 1]) {
                 uint64_t key = row_key<P>(c, x, w, rt);
-                if ((!has_cut || key > cut) && key < t[RC - 1]) {
-                    t[RC - 1] = key;
+                if ((!has_cut || key > cut) && key < t[K - 1]) {
+                    t[K - 1] = key;
 #pragma unroll
-                    for (int r = RC - 1; r > 0; --r) {
+                    for (int r = K - 1; r > 0; --r) {
                         const uint64_t lo = t[r - 1] < t[r] ? t[r - 1] : t[r], hi = t[r - 1] < t[r] ? t[r] : t[r - 1];
                         t[r - 1] = lo;
                         t[r] = hi;
@@ -156,14 +146,14 @@ __device__ void warp_rows_above(const Ctx& c, const Simplex<P>& x, bool has_cut,
         }
     }
 #pragma unroll
-    for (int r = 0; r < RC; ++r) {
+    for (int r = 0; r < K; ++r) {
         const uint64_t m = warp_min_u64(t[0]);
         out[r] = m;
         const uint32_t own = __ballot_sync(0xffffffffu, m != EMPTY && t[0] == m);
         if (own && lane == __ffs(own) - 1) {  // keys of one coboundary are distinct: one owner
 #pragma unroll
-            for (int q = 0; q < RC - 1; ++q) t[q] = t[q + 1];
-            t[RC - 1] = EMPTY;
+            for (int q = 0; q < K - 1; ++q) t[q] = t[q + 1];
+            t[K - 1] = EMPTY;
         }
     }
 }
@@ -992,16 +982,6 @@ __device__ bool heavy_cob_place(HeavySmem& S, uint64_t* B, int64_t bcap, bool ok
 
 template <int P, bool GROUP = false>
 __device__ int heavy_owner_probe(const Ctx& c, HeavySmem& S, uint64_t rk, uint64_t self_key);
-
-// True if x is in the sorted array a[0..len).
-__device__ __forceinline__ bool sorted_has(const uint64_t* a, int len, uint64_t x) {
-    int lo = 0, hi = len;
-    while (lo < hi) {
-        const int m = (lo + hi) >> 1;
-        if (a[m] < x) lo = m + 1; else hi = m;
-    }
-    return lo < len && a[lo] == x;
-}
 
 // heavy_cob_place for the last (here: only) pass of an addition, with the
 // owner probe of the next pivot overlapped with the merge.  The next pivot
