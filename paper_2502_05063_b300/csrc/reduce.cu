@@ -203,16 +203,16 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
     long long t0 = clock64(), t_ref = 0, t_look = 0, t_add = 0, n_look = 0;
     const long long t_resume = t0;
     while (ok) {
-        long long ta = clock64();
+        long long ta = HCLK();
         if (S.fsize == 0 && !heavy_refill(S, B)) { key = EMPTY; break; }  // zero column
-        long long tb = clock64();
+        long long tb = HCLK();
         t_ref += tb - ta;
         key = S.buf[S.cur][0];
         // the owner of this pivot may have been probed during the last merge
         const int kind = pre ? (pre == 3 ? 0 : pre) : heavy_owner_probe<P>(c, S, key, self_key);
         if (pre && threadIdx.x == 0 && key != S.sel) atomicExch(c.err, DEV_INTERNAL | (1 << 8));
         pre = 0;
-        long long tc = clock64();
+        long long tc = HCLK();
         t_look += tc - tb;
         ++n_look;
         if (kind == 0) break;  // pivot unknown: complete
@@ -248,7 +248,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
         ++done;
         __syncthreads();
         if (hs.prof && threadIdx.x == 0) S.tp[15] += clock64();
-        t_add += clock64() - tc;
+        t_add += HCLK() - tc;
     }
     if (hs.prof && threadIdx.x == 0) {
         atomicAdd(hs.prof + 0, (unsigned long long)t_ref);

@@ -468,8 +468,18 @@ struct HeavySmem {
     uint64_t sel;          // the next pivot, when found during a merge
     long long tp[20];      // VR_LOG only (thread 0): sub-phase cycles
 };
+// Sub-phase cycle counters of the block engine (thread 0, into S.tp), printed
+// with VR_LOG=1; compiled in only with -DVR_HPROF, since their clock reads sit
+// on the per-addition critical path.
+#ifdef VR_HPROF
+#define HCLK() clock64()
 #define HPROF_T0() long long _hp_t = clock64()
 #define HPROF_LAP(i) do { if (threadIdx.x == 0) { long long _n = clock64(); S.tp[i] += _n - _hp_t; _hp_t = _n; } } while (0)
+#else
+#define HCLK() 0ll
+#define HPROF_T0() do { } while (0)
+#define HPROF_LAP(i) do { } while (0)
+#endif
 
 // exclusive block scan of one int per thread; *total receives the sum.
 // Warp scans, one barrier to publish the warp totals, then every warp sums
@@ -1021,13 +1031,17 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
     const int cur = S.cur, a = S.fsize;  // read by every thread before the groups part
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (wid >= 2) {
+#ifdef VR_HPROF
         const long long tm = clock64();
+#endif
         const int na = merge_group(S, srt, cur, a, nlt, 64, HT - 64, 1);
         if (threadIdx.x == 64) {
+#ifdef VR_HPROF
             S.tp[16] += clock64() - tm;  // merge group alone
             S.tp[17] += a;
             S.tp[18] += nlt;
             S.tp[19] += 1;
+#endif
             S.na = na;
             S.cur = cur ^ 1;
             S.fsize = min(na, FKEEP);
