@@ -444,7 +444,8 @@ struct HeavyState {
     unsigned long long* prof;  // VR_LOG only: cycles {refill, lookup, add, resume}, counts {adds, lookups}
 };
 
-// VR_LOG instrumentation of the block engine: {refills, rows to front, rows to back, merges}
+// VR_LOG instrumentation of the block engine (-DVR_HPROF builds): {refills, rows to front, rows
+// to back, merges}
 __device__ unsigned long long g_heavy_counts[4];
 
 struct HeavySmem {
@@ -776,7 +777,9 @@ __device__ bool heavy_refill(HeavySmem& S, uint64_t* B) {
         const int64_t bsz = S.bsize;
         if (bsz == 0) return false;
         HPROF_T0();
+#ifdef VR_HPROF
         if (threadIdx.x == 0) { atomicAdd(&g_heavy_counts[0], 1ull); S.tp[9] += 1; }
+#endif
         uint64_t* Sm = S.buf[S.cur];  // the sample (the front is empty), then the gathered rows
         uint32_t* P = reinterpret_cast<uint32_t*>(S.buf[S.cur ^ 1]);  // positions of the rows below Tb (2 FC)
         uint64_t Ta = EMPTY, Tb = EMPTY;
@@ -977,9 +980,11 @@ __device__ bool heavy_cob_place(HeavySmem& S, uint64_t* B, int64_t bcap, bool ok
     if (lt) S.stage[packed & 0xFFFF] = key;
     if (threadIdx.x == 0) {
         S.bsize = bs + nge;
+#ifdef VR_HPROF
         atomicAdd(&g_heavy_counts[1], (unsigned long long)nlt);
         atomicAdd(&g_heavy_counts[2], (unsigned long long)nge);
         atomicAdd(&g_heavy_counts[3], 1ull);
+#endif
     }
     __syncthreads();
     HPROF_LAP(0);
@@ -1018,9 +1023,11 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
     if (threadIdx.x == 0) {
         S.bsize = bs + nge;
         S.pkind = 0;
+#ifdef VR_HPROF
         atomicAdd(&g_heavy_counts[1], (unsigned long long)nlt);
         atomicAdd(&g_heavy_counts[2], (unsigned long long)nge);
         atomicAdd(&g_heavy_counts[3], 1ull);
+#endif
     }
     __syncthreads();
     HPROF_LAP(0);
