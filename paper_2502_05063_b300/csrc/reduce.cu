@@ -421,9 +421,10 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         // Columns are finalized between rounds only, so a round that runs as
         // long as its longest column would keep columns it unblocks idle; a
         // cap of 64 additions (about 0.3 ms) keeps rounds short.  With at most
-        // four unfinished columns few can be waiting, and rounds of up to 256
-        // additions save launches, state reloads and finalizations (measured:
-        // torus500's two long dimension-1 columns, 10.0 -> 9.65 ms).
+        // eight unfinished columns few can be waiting, and rounds of up to 256
+        // additions save launches, state reloads and finalizations (measured on
+        // torus500: its two long dimension-1 columns, 10.0 -> 9.65 ms with the
+        // bound at four; dimension 2, 8.99 -> 8.85 ms with it at eight).
         constexpr int budget_cap = 64, budget_cap_few = 256;
         int64_t stalled_adds = 0;  // additions granted to the first column since a column was last finalized
         cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -455,7 +456,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 cur ^= 1;
                 ++rounds;
                 granted += budget;
-                const int cap = u0 <= 4 ? budget_cap_few : budget_cap;
+                const int cap = u0 <= 8 ? budget_cap_few : budget_cap;
                 budget = budget < cap ? 2 * budget : cap;
             }
             VR_CUDA(cudaMemcpyAsync(&hs.p[8], du + cur, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
