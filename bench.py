@@ -14,6 +14,17 @@ workload), divided by the whole step time.  `value` times steps on inputs
 already resident on the device; `e2e` times the same call on pinned host
 input, host-to-device copy and result copy inside the timed region.
 
+Further keys: `roofline` -- the fused filtration/apparent kernel of the top
+dimension, its algorithmic bytes per launch (per-unit figures of the
+filtration and apparent steps, see roofline_bytes) over its CUDA-event time,
+against the measured HBM copy bandwidth and a project-written L2 read probe;
+`cpu_baseline` -- the oracle on a bounded sample of the same workload (the
+same cloud, dimensions 0-1), single thread, median of 5; `batched` -- the
+4096-cloud forward and the 256-circle forward+backward (median of 20 and the
+spread), each against a per-cloud loop of the same library, with the oracle
+on all host cores beside them (`cpu_baseline_batched`); `other_workloads` --
+stage rates of the 64-point uniform and 200-point sphere workloads.
+
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 (torchrun), single clouds do not shard: every rank runs a replica
 and the value is the work of all ranks over the slowest rank's time.
@@ -37,9 +48,11 @@ WORKLOAD = "torus500"
 METRIC = "simplices/sec filtration+apparent-pairs; batched VR fwd+bwd clouds/sec vs plain"
 UNIT = "simplices/s"
 L2_FLUSH_BYTES = 256 << 20
-# oracle sample for the CPU baseline: the same torus generator at fewer points
-CPU_SAMPLE_N = 320
-REF_STEP_N = 140
+# The oracle's bounded sample of the benched workload: the same 500-point torus
+# cloud (seed 1), dimensions 0-1 (the whole H0-H2 computation takes the oracle
+# about two minutes).  Rate = dimension-1 candidates C(500, 2) per second.
+CPU_SAMPLE_DMAX = 1
+CPU_SAMPLE_REPEATS = 5
 
 
 def candidates(n: int, dmax: int) -> int:
@@ -112,21 +125,139 @@ def count_launches(fn):
     return n
 
 
-def cpu_oracle_throughput(n: int):
-    """The oracle as it stands (single thread) on the same generator at n points."""
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_sample_seconds(pts, dmax):
+    """One run of the oracle as it stands (single thread, cohomology with
+    clearing), distances and enclosing radius included, input generation not."""
     import numpy as np
     import oracle
-    from paper_2502_05063_b300 import synth
-    pts = synth.torus(n, seed=1)
+    n = pts.shape[0]
     t0 = time.perf_counter()
     D = oracle.distances_f32(pts).astype(np.float64)
     R = oracle.enclosing_radius(D, n)
-    oracle.cohom(D, n, 2, R, clearing=True)
-    dt = time.perf_counter() - t0
-    return candidates(n, 2) / dt, dt
+    oracle.cohom(D, n, dmax, R, clearing=True)
+    return time.perf_counter() - t0
 
 
-def batched_metrics(stream, steps=3):
+def cpu_baseline_single(repeats=CPU_SAMPLE_REPEATS):
+    """Median of `repeats` oracle runs on the bounded sample, after one warm-up."""
+    import oracle
+    from paper_2502_05063_b300 import synth
+    oracle.build()
+    pts = synth.WORKLOADS[WORKLOAD]["make"]()
+    n = pts.shape[0]
+    oracle_sample_seconds(pts, CPU_SAMPLE_DMAX)
+    times = [oracle_sample_seconds(pts, CPU_SAMPLE_DMAX) for _ in range(repeats)]
+    med = statistics.median(times)
+    return {"value": candidates(n, CPU_SAMPLE_DMAX) / med, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds_median": med, "seconds_all": times, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "sample": "oracle (plain C, cohomology with clearing, single thread) on the benched 500-point torus "
+                      "cloud (seed 1, enclosing radius), dimensions 0-1: C(500,2) = 124,750 candidate simplices "
+                      "per run; median of %d runs after one warm-up" % repeats}
+
+
+def cpu_baseline_batched():
+    """The oracle on bounded samples of the two batched workloads, one cloud per
+    process on all host cores (spawn-started pool, warmed before timing)."""
+    from oracle import pool as opool
+    from paper_2502_05063_b300 import synth
+    procs = os.cpu_count() or 1
+    clouds, _ = synth.batch_clouds()
+    c4 = clouds[::32]
+    circ = synth.circles()
+    c5 = circ[::4]
+    with opool.open_pool(procs) as pl:
+        opool.diagrams(c4[:procs], 1, pool=pl)  # warm the workers (imports, library load)
+        t0 = time.perf_counter()
+        opool.diagrams(c4, 1, pool=pl)
+        t4 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        opool.loss_grads(c5, 1, pl)
+        t5 = time.perf_counter() - t0
+    return {
+        "batch4096_forward": {"clouds_per_s": len(c4) / t4, "cores": procs, "kind": "oracle", "seconds": t4,
+                              "sample": "every 32nd cloud of the 4096-cloud workload (%d clouds), H0-H1, "
+                                        "one cloud per process" % len(c4)},
+        "circles256_fwd_bwd": {"clouds_per_s": len(c5) / t5, "cores": procs, "kind": "oracle", "seconds": t5,
+                               "sample": "every 4th cloud of the 256-circle workload (%d clouds): pairing "
+                                         "(cohomology) plus the FP64 gradient of sum over H1 of (death-birth)^2, "
+                                         "one cloud per process" % len(c5)},
+        "cpu_model": cpu_model(),
+    }
+
+
+def roofline_bytes(p, st):
+    """Algorithmic bytes of one launch of the fused filtration/apparent kernel of
+    dimension p, by the per-unit figures of the filtration and apparent steps:
+      filtration (Alg 17/18): per candidate C(p+1,2) 4-byte diameter lookups and
+        one clearing bit; per kept column an 8-byte key;
+      apparent search (Lemma 5.3.6): per kept column an 8-byte key read, up to
+        16 bytes of output and (p+2) C(p+1,2) 4-byte lookups for the facet test;
+        per cofacet examined (p+1) 4-byte lookups."""
+    cand, kept, cof = st["candidates"], st["columns"], st["cofacets_scanned"]
+    pairs = (p + 1) * p // 2
+    a3 = cand * pairs * 4 + cand / 8.0 + kept * 8
+    a5 = kept * (8 + 16 + (p + 2) * pairs * 4) + cof * (p + 1) * 4
+    return a3 + a5, {"filtration": a3, "apparent": a5}
+
+
+def stage_rates_of(stats, dmax, stage):
+    dims = range(1, dmax + 1)
+    f_ms = sum(stage["dim%d" % p]["ms_filtration"] for p in dims)
+    s_ms = sum(stage["dim%d" % p]["ms_sort"] for p in dims)
+    return {
+        "filtration_simplices_per_s": (sum(stats[p]["candidates"] for p in dims) / ((f_ms + s_ms) / 1e3)
+                                       if f_ms + s_ms > 0 else None),
+        "apparent_columns_per_s": sum(stats[p]["columns"] for p in dims) / (f_ms / 1e3) if f_ms > 0 else None,
+        "cofacets_per_s": sum(stats[p]["cofacets_scanned"] for p in dims) / (f_ms / 1e3) if f_ms > 0 else None,
+    }
+
+
+def other_workload_rates(stream, reps=5):
+    """M1/M2 stage rates of the 64-point uniform and 200-point sphere workloads
+    (library stage timers, mean over `reps` calls after two warm-up calls)."""
+    from paper_2502_05063_b300 import synth, vr
+    import torch
+    out = {}
+    for name in ("uniform64", "sphere200"):
+        w = synth.WORKLOADS[name]
+        x = torch.from_numpy(w["make"]()).cuda()
+        dmax = w["dmax"]
+        for _ in range(2):
+            vr.barcodes(points=x, dmax=dmax, threshold=w["threshold"], stream=stream)
+        rs = [vr.barcodes(points=x, dmax=dmax, threshold=w["threshold"], stream=stream) for _ in range(reps)]
+        stage = {"dim%d" % p: {k: statistics.mean(r.stats[p][k] for r in rs)
+                               for k in ("ms_filtration", "ms_sort", "ms_reduce")} for p in range(dmax + 1)}
+        rates = stage_rates_of(rs[-1].stats, dmax, stage)
+        rates["stages_ms"] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in stage.items()}
+        rates["counts"] = {"dim%d" % p: {k: rs[-1].stats[p][k] for k in ("candidates", "columns", "apparent",
+                                                                           "reduced", "additions", "cofacets_scanned")}
+                           for p in range(1, dmax + 1)}
+        rates["workload"] = w["desc"]
+        out[name] = rates
+    return out
+
+
+def probe_peaks(stream):
+    """Project-written read probes (vr_probe_read_gbs): L2-resident and HBM."""
+    from paper_2502_05063_b300 import vr
+    l2 = max(vr.probe_read_gbs(mb << 20, 200, stream) for mb in (16, 32, 48))
+    hbm = vr.probe_read_gbs(4 << 30, 10, stream)
+    return {"l2_read_gbs": l2, "hbm_read_gbs": hbm,
+            "how": "vr_probe_read_gbs: 16-byte ld.global.cg loads over 4 blocks of 512 threads per SM; L2: best of "
+                   "16/32/48 MB buffers x 200 passes; HBM: 4 GB x 10 passes; CUDA events, one untimed pass first"}
+
+
+def batched_metrics(stream, steps=20):
     """The batched forms: 4096 clouds (forward, H0-H1) and 256 clouds of 128
     points in R^2 (forward + backward of sum (death - birth)^2 over H1), each in
     clouds/s, against a loop of per-cloud calls of the same library."""
@@ -134,22 +265,29 @@ def batched_metrics(stream, steps=3):
     from paper_2502_05063_b300 import autograd, synth, vr
 
     def timeit(fn, k):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(k):
+        """Median ms of k timed calls (CUDA events per call) after 3 warm-up calls, and the spread."""
+        for _ in range(3):
             fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1) / k
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ms.sort()
+        spread = {"min": ms[0], "p10": ms[len(ms) // 10], "median": statistics.median(ms),
+                  "p90": ms[(9 * len(ms)) // 10], "max": ms[-1], "repeats": k}
+        return statistics.median(ms), spread
 
     clouds, _ = synth.batch_clouds()
     pts, offs = synth.pack(clouds)
     dev = torch.from_numpy(pts).cuda()
-    fwd_ms = timeit(lambda: vr.barcodes_batched(dev, offs, dmax=1, stream=stream), steps)
+    fwd_ms, fwd_spread = timeit(lambda: vr.barcodes_batched(dev, offs, dmax=1, stream=stream), steps)
     sample = [torch.from_numpy(c).cuda() for c in clouds[::32]]
-    loop_ms = timeit(lambda: [vr.barcodes(points=d, dmax=1, stream=stream) for d in sample], 1) / len(sample)
+    loop_ms = timeit(lambda: [vr.barcodes(points=d, dmax=1, stream=stream) for d in sample], 3)[0] / len(sample)
 
     circ = synth.circles()
     cp, co = synth.pack(circ)
@@ -171,14 +309,16 @@ def batched_metrics(stream, steps=3):
             fin = torch.isfinite(h1[:, 1])
             ((h1[fin, 1] - h1[fin, 0]) ** 2).sum().backward()
 
-    fb_ms = timeit(fwd_bwd_batched, steps)
-    fb_loop_ms = timeit(fwd_bwd_loop, 1) / len(singles)
+    fb_ms, fb_spread = timeit(fwd_bwd_batched, steps)
+    fb_loop_ms = timeit(fwd_bwd_loop, 3)[0] / len(singles)
     return {
         "batch4096_forward": {"clouds_per_s": len(clouds) / (fwd_ms / 1000), "ms_per_batch": fwd_ms,
+                              "ms_spread": fwd_spread,
                               "per_cloud_loop_clouds_per_s": 1000 / loop_ms, "speedup_vs_loop": loop_ms * len(clouds) / fwd_ms,
                               "workload": "4096 clouds, n~U{32..256}, circle/sphere/cube in R^3, H0-H1, seed 3",
                               "loop_sample": "every 32nd cloud, one vr_barcodes call each"},
         "circles256_fwd_bwd": {"clouds_per_s": len(circ) / (fb_ms / 1000), "ms_per_batch": fb_ms,
+                               "ms_spread": fb_spread,
                                "per_cloud_loop_clouds_per_s": 1000 / fb_loop_ms,
                                "speedup_vs_loop": fb_loop_ms * len(circ) / fb_ms,
                                "workload": "256 noisy circles, n=128 in R^2, sigma 0.1, seed 4; loss sum over H1 of "
@@ -188,27 +328,34 @@ def batched_metrics(stream, steps=3):
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands (the paper ships no code), on the
+    host cores, each step one bounded sample of the benched workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
+    from paper_2502_05063_b300 import synth
     oracle.build()
+    pts = synth.WORKLOADS[WORKLOAD]["make"]()
+    n = pts.shape[0]
     for _ in range(args.warmup):
-        cpu_oracle_throughput(REF_STEP_N)
+        oracle_sample_seconds(pts, CPU_SAMPLE_DMAX)
     t0 = time.perf_counter()
     total = 0.0
     for _ in range(args.steps):
-        _, dt = cpu_oracle_throughput(REF_STEP_N)
-        total += dt
+        total += oracle_sample_seconds(pts, CPU_SAMPLE_DMAX)
     wall = time.perf_counter() - t0
-    value = candidates(REF_STEP_N, 2) * args.steps / total
-    sample = ("oracle (plain C, cohomology with clearing, single thread) on the torus generator at n=%d "
-              "(seed 1, H0-H2, enclosing radius) per step" % REF_STEP_N)
+    value = candidates(n, CPU_SAMPLE_DMAX) * args.steps / total
+    sample = ("oracle (plain C, cohomology with clearing, single thread) on the benched 500-point torus cloud "
+              "(seed 1, enclosing radius), dimensions 0-1 per step: C(500,2) = 124,750 candidate simplices")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample_n": REF_STEP_N},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "ambient_dim": 3, "dmax": 2, "threshold": "enclosing radius",
+                       "reference_sample": "dimensions 0-1 of the same cloud"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line))
@@ -285,22 +432,23 @@ def run_ours(args):
     d2h += 24 * (n + sum(last.stats[p]["reduced"] for p in range(1, dmax + 1)))  # device pair records read back
     d2h += 4 * (n * (n - 1) // 2 + 1)  # diameter value table (upper bound)
 
-    # roofline of the fused filtration/apparent kernel of the top dimension: integer-issue bound
-    # (ncu: issue ~73%, ALU pipe ~66%, L1 ~21%, DRAM a few MB); one algorithmic op = one
-    # diameter-rank lookup and comparison, counted by the kernel (candidate diameters, p+1 per
-    # examined cofacet, all pairs of t per facet test)
+    # Roofline of the fused filtration/apparent kernel of the top dimension: its
+    # algorithmic bytes (roofline_bytes) over its CUDA-event time per launch
+    # (the library's stage timer around that launch, on the call's stream),
+    # against the measured HBM copy bandwidth and the probed L2 read bandwidth.
     peaks, peak_src = load_peaks()
+    probes = probe_peaks(stream)
     st = last.stats[dmax]
     fa_ms = statistics.mean(r.stats[dmax]["ms_filtration"] for r in results)
-    ops = st["lookups"]
-    achieved = ops / (fa_ms / 1000.0) / 1e9
-    sm_max = peaks.get("sm_max_mhz", 2032.0)
-    alu_peak = 148 * 128 * sm_max * 1e6 / 1e9  # INT32 lane operations per second, in G
+    nbytes, parts = roofline_bytes(dmax, st)
+    achieved = nbytes / (fa_ms / 1000.0) / 1e9
+    hbm_peak = float(peaks["hbm_gbs"])
     stage = {}
     for p in range(dmax + 1):
         stage["dim%d" % p] = {k: round(statistics.mean(r.stats[p][k] for r in results), 4)
                               for k in ("ms_filtration", "ms_sort", "ms_reduce")}
     traffic = None
+    issue = None
     prof = os.path.join(ROOT, "profiles", "traffic_filtration_apparent_torus500.json")
     if os.path.exists(prof):
         try:
@@ -311,23 +459,19 @@ def run_ours(args):
                            for f in ("apparent.cu", "vr_common.cuh"))
             if rec.get("source_sha256") == hashlib.sha256(src).hexdigest():
                 traffic = rec.get("bytes_per_launch")
+                if rec.get("warp_instructions"):
+                    issue = {"warp_instructions_per_launch": rec["warp_instructions"],
+                             "lookups_per_launch": st["lookups"],
+                             "thread_instructions_per_lookup": rec["warp_instructions"] * rec.get("active_lanes", 32)
+                             / max(st["lookups"], 1),
+                             "active_lanes_per_instruction": rec.get("active_lanes"),
+                             "issue_active_pct": rec.get("issue_active_pct"),
+                             "source": "ncu capture recorded in profiles/ (same kernel source)"}
         except (OSError, ValueError):
             traffic = None
 
-    # the stage rates of the method's data-parallel steps (library stage timers of the last
-    # timed calls): filtration simplices over filtration + sort time, apparent-search columns
-    # and cofacets over the fused filtration/apparent kernel's time
-    dims = range(1, dmax + 1)
-    f_ms = sum(stage["dim%d" % p]["ms_filtration"] for p in dims)
-    s_ms = sum(stage["dim%d" % p]["ms_sort"] for p in dims)
-    stage_rates = {
-        "filtration_simplices_per_s": (sum(last.stats[p]["candidates"] for p in dims) / ((f_ms + s_ms) / 1e3)
-                                       if f_ms + s_ms > 0 else None),
-        "apparent_columns_per_s": (sum(last.stats[p]["columns"] for p in dims) / (f_ms / 1e3)
-                                   if f_ms > 0 else None),
-        "cofacets_per_s": sum(last.stats[p]["cofacets_scanned"] for p in dims) / (f_ms / 1e3) if f_ms > 0 else None,
-        "note": "dimensions 1-%d; filtration and apparent search run as one fused kernel" % dmax,
-    }
+    stage_rates = stage_rates_of(last.stats, dmax, stage)
+    stage_rates["note"] = "dimensions 1-%d; filtration and apparent search run as one fused kernel" % dmax
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -339,25 +483,30 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": launches * args.steps,
-        "roofline": {"kernel": "k_filtration_apparent<%d>" % dmax, "bound": "alu",
-                     "achieved": achieved, "peak": alu_peak, "unit": "Gop/s", "frac": achieved / alu_peak,
-                     "traffic": traffic, "ms_per_launch": fa_ms, "ops_per_launch": ops,
-                     "peak_source": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz (%s sm_max)" % (sm_max, peak_src),
-                     "op": "one diameter-rank lookup and comparison"},
+        "roofline": {"kernel": "k_filtration_apparent<%d>" % dmax, "bound": "hbm",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": traffic, "ms_per_launch": fa_ms, "algorithmic_bytes_per_launch": nbytes,
+                     "bytes_by_step": parts,
+                     "peak_source": "hbm_gbs of MEASURED_PEAKS.json (%s; burst copy)" % peak_src,
+                     "l2": {"peak": probes["l2_read_gbs"], "frac": achieved / probes["l2_read_gbs"],
+                            "peak_source": "project L2-resident read probe, this run"},
+                     "target_frac": 0.5},
+        "peaks_probe": probes,
+        "issue": issue,
         "stages_ms": stage,
         "stage_rates": stage_rates,
         "clocks": clk,
         "counts": {"dim%d" % p: {k: last.stats[p][k] for k in ("candidates", "columns", "apparent", "reduced",
-                                                                 "additions", "cofacets_scanned")}
+                                                                 "additions", "cofacets_scanned", "lookups")}
                    for p in range(1, dmax + 1)},
     }
     if not args.no_batched:
         line["batched"] = batched_metrics(stream)
+        line["other_workloads"] = other_workload_rates(stream)
     if world == 1 and not args.no_cpu_baseline:
-        v, dt = cpu_oracle_throughput(CPU_SAMPLE_N)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
-                                "sample": "oracle (plain C, cohomology with clearing, single thread) on the same "
-                                          "torus generator at n=%d, H0-H2, enclosing radius" % CPU_SAMPLE_N}
+        line["cpu_baseline"] = cpu_baseline_single()
+        if not args.no_batched:
+            line["cpu_baseline_batched"] = cpu_baseline_batched()
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -30,8 +30,10 @@
  *    results are on the host.
  *  - On error nothing is written to *out (it is set to NULL) and the call
  *    returns a nonzero vr_status; vr_status_string() names it.
- *  - Every device-side wait in the library is bounded; exhausting a bound
- *    returns VR_ERR_TIMEOUT instead of hanging.
+ *  - No kernel of the library waits on another thread block: the rounds of
+ *    the reduction synchronise at kernel boundaries on the host, so there is
+ *    no device-side wait to time out.  VR_ERR_TIMEOUT is reserved and is not
+ *    returned by any entry point.
  */
 #ifndef VR_H
 #define VR_H
@@ -51,13 +53,19 @@ typedef enum {
     VR_ERR_OOM = 2,             /* a device or host allocation failed                              */
     VR_ERR_INDEX_OVERFLOW = 3,  /* C(n, dmax+2) or a packed sort key does not fit 64 bits           */
     VR_ERR_CUDA = 4,            /* a CUDA runtime call failed (no device, launch failure, ...)      */
-    VR_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out                               */
+    VR_ERR_TIMEOUT = 5,         /* reserved: no entry point returns it (no device-side waits)       */
     VR_ERR_INTERNAL = 6         /* an internal consistency check failed                             */
 } vr_status;
 
 /* flags */
 #define VR_KEEP_ZERO_LENGTH 0x1u /* also report pairs with death == birth                     */
 #define VR_CRITICAL_EDGES   0x2u /* fill vr_result.critical_edges (needed by vr_backward)     */
+#define VR_DEBUG_CHECKS     0x4u /* check identities every correct result satisfies before
+                                    returning (Obs 3.2.14 counts per dimension: each simplex
+                                    within the threshold is a birth or a death; cleared
+                                    columns = death simplices one dimension down; birth <=
+                                    death; documented pair order); a violation returns
+                                    VR_ERR_INTERNAL.  Host-side, after the computation.     */
 
 /* One persistence pair of dimension p.  birth = diam(birth simplex),
  * death = diam(death simplex) or +INFINITY for an essential class. */
@@ -105,7 +113,11 @@ typedef struct {
 
 /* Barcodes of a point cloud.
  *  pts        float[n][ambient_dim], row-major, host or device.
- *  n          number of points, 1 <= n <= 2^20 (and C(n, dmax+2) < 2^63).
+ *  n          number of points, 1 <= n <= 65536.  C(n, dmax+2) >= 2^63 returns
+ *             VR_ERR_INDEX_OVERFLOW before any device work; so does a dimension
+ *             whose packed keys (diameter rank above a simplex index, Sec. 5.5.2)
+ *             would not fit 64 bits, checked once the distinct distances are
+ *             ranked and before the first dimension is computed.
  *  ambient_dim 1..1024.
  *  dmax       0..VR_MAX_DIM.
  *  threshold  see above; must not be NaN.  threshold < 0 gives an empty result.
@@ -152,7 +164,12 @@ void vr_batch_result_free(vr_batch_result* r);
  *  pts        float[n][ambient_dim], device pointer.
  *  edges      int32[num][4] (u_b, v_b, u_d, v_d), device pointer (-1 = no edge).
  *  grad_birth, grad_death  float[num], device pointers.
- *  grad_pts   float[n][ambient_dim], device pointer, accumulated into (+=).     */
+ *  grad_pts   float[n][ambient_dim], device pointer, accumulated into (+=).
+ * An edge endpoint outside 0..n-1 (other than -1) returns VR_ERR_INVALID_ARG;
+ * that edge contributes nothing, the valid edges still accumulate.
+ * The forward result is passed as its critical-edge array (not as the
+ * vr_result) so that edges kept on the device by the torch path, and the
+ * packed edges of a batched result, use this same entry point.           */
 vr_status vr_backward(const float* pts, int64_t n, int32_t ambient_dim, const int32_t* edges,
                       int64_t num, const float* grad_birth, const float* grad_death,
                       float* grad_pts, void* stream);
@@ -190,7 +207,19 @@ vr_status vr_sort_u64(uint64_t* keys, uint64_t* values, int64_t num, int32_t bit
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the one array: calls whose
  * work overlaps on the GPU (several streams or host threads) race and must be
- * serialised by the caller.  Returns after `stream` has finished the sort.  */
+ * serialised by the caller.  Every call synchronises `stream` before it
+ * returns (the sort is finished on return), so no call of it may be made
+ * while `stream` is being captured into a CUDA graph.                       */
+/* Read-bandwidth probe for the roofline denominators (the paper has no
+ * counterpart).  Streams a zeroed device buffer of `bytes` bytes `iters`
+ * times with 16-byte loads that bypass L1, on `stream`, and writes the read
+ * bandwidth in GB/s (10^9 bytes per second, CUDA-event timed, after one
+ * untimed pass) to *out_gbs.  A buffer well inside the 126 MB L2 measures
+ * L2 read bandwidth; one far larger measures HBM read bandwidth.  The buffer
+ * is allocated and freed on `stream`; nothing else is touched.
+ *  bytes      2^20 .. 2^36;  iters 1 .. 100000.                             */
+vr_status vr_probe_read_gbs(int64_t bytes, int32_t iters, void* stream, double* out_gbs);
+
 #define VR_SORT_NOALLOC_MAX_KEYS (1 << 18)
 vr_status vr_sort_u64_noalloc(uint64_t* keys, uint64_t* values, int64_t num, int32_t bits, void* stream);
 

@@ -277,6 +277,36 @@ static void fill_dim(vr_result* res, int p, const HostPairs& hp, const std::vect
     res->stats[p].emitted = m;
 }
 
+// VR_DEBUG_CHECKS: identities every correct result satisfies, from the
+// counters and the emitted pairs.  Obs 3.2.14: each p-simplex of the complex
+// is a birth (paired or essential) or the death of a (p-1)-class; here the
+// p-simplices within the threshold are the kept columns plus the cleared ones,
+// the cleared ones are exactly the death simplices of the (p-1)-pairs
+// (Sec. 5.2.3), and every kept column is paired or essential.  Each emitted
+// pair has birth <= death, and the pairs are sorted as documented.
+static void debug_checks(const vr_result* res) {
+    for (int p = 0; p <= res->dmax; ++p) {
+        const vr_stats& st = res->stats[p];
+        VR_CHECK(st.columns == st.pairs + st.essential, VR_ERR_INTERNAL);
+        if (p >= 1) {
+            VR_CHECK(st.cleared == res->stats[p - 1].pairs, VR_ERR_INTERNAL);
+            VR_CHECK(st.candidates == st.above_threshold + st.cleared + st.columns, VR_ERR_INTERNAL);
+            VR_CHECK(st.reduced + st.apparent <= st.columns, VR_ERR_INTERNAL);
+        }
+        for (int64_t k = 0; k < res->count[p]; ++k) {
+            const vr_pair& a = res->pairs[p][k];
+            VR_CHECK(a.birth <= a.death && a.birth >= 0.0f, VR_ERR_INTERNAL);
+            VR_CHECK((a.death_simplex < 0) == std::isinf(a.death), VR_ERR_INTERNAL);
+            if (k > 0) {
+                const vr_pair& b = res->pairs[p][k - 1];
+                const bool ordered = b.birth < a.birth || (b.birth == a.birth && (b.death < a.death ||
+                                     (b.death == a.death && b.birth_simplex <= a.birth_simplex)));
+                VR_CHECK(ordered, VR_ERR_INTERNAL);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the driver
 // ---------------------------------------------------------------------------
@@ -315,6 +345,16 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
     const Binom B{db, n, K};
     VR_CUDA(cudaStreamSynchronize(s));  // host binomial vector and values copy
     if (isinf(threshold) && threshold > 0) res->threshold = values[thr];
+
+    // every dimension's packed keys must fit before any work starts: a column key
+    // holds the diameter rank above the p-simplex index, a row key the rank above
+    // the (p+1)-simplex index
+    for (int p = 1; p <= dmax; ++p) {
+        const uint64_t ncand = binom_host(n, p + 1), nrow = binom_host(n, p + 2);
+        const int cb = std::max(1, bits_for(ncand > 0 ? ncand - 1 : 0));
+        const int rcb = std::max(1, bits_for(nrow > 0 ? nrow - 1 : 0));
+        VR_CHECK(nrow != UINT64_MAX && rank_bits + cb <= 64 && rank_bits + rcb <= 63, VR_ERR_INDEX_OVERFLOW);
+    }
 
     int* dev_err = ws.zeros_n<int>(1);
     unsigned long long* cnt = ws.zeros_n<unsigned long long>(16);
@@ -438,6 +478,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         res->stats[p].ms_reduce = log.between(stage_name("launch reduce", p), stage_name("reduce", p));
     }
     if (log_enabled()) log.print();
+    if (flags & VR_DEBUG_CHECKS) debug_checks(res);
     guard.r = nullptr;
     return res;
 }
@@ -449,7 +490,9 @@ static vr_status run_guarded(vr_result** out, const float* data, bool is_points,
     if (!data && n > 1) return VR_ERR_INVALID_ARG;
     if (n < 1 || n > (1 << 16) || dmax < 0 || dmax > VR_MAX_DIM || std::isnan(threshold)) return VR_ERR_INVALID_ARG;
     if (is_points && (amb < 1 || amb > 1024)) return VR_ERR_INVALID_ARG;
-    if (flags & ~(uint32_t)(VR_KEEP_ZERO_LENGTH | VR_CRITICAL_EDGES)) return VR_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)(VR_KEEP_ZERO_LENGTH | VR_CRITICAL_EDGES | VR_DEBUG_CHECKS)) return VR_ERR_INVALID_ARG;
+    // simplex indices of dimension dmax+1 must fit 63 bits (checked before any device work)
+    if (binom_host(n, dmax + 2) >= (1ull << 63)) return VR_ERR_INDEX_OVERFLOW;
     try {
         cudaStream_t s = (cudaStream_t)stream;
         Workspace ws(s);

@@ -14,14 +14,21 @@
 
 namespace vr {
 
-__global__ void k_backward(const float* __restrict__ pts, int dim, const int32_t* __restrict__ edges, int64_t num,
-                           const float* __restrict__ gb, const float* __restrict__ gd, float* __restrict__ grad) {
+// An edge with an endpoint outside 0..n-1 is skipped and reported through
+// *dev_err (the host returns VR_ERR_INVALID_ARG); -1 marks "no edge".
+__global__ void k_backward(const float* __restrict__ pts, int64_t n, int dim, const int32_t* __restrict__ edges,
+                           int64_t num, const float* __restrict__ gb, const float* __restrict__ gd,
+                           float* __restrict__ grad, int* dev_err) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 2 * num;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t pair = k >> 1;
         const int which = (int)(k & 1);  // 0 = birth edge, 1 = death edge
         const int u = edges[4 * pair + 2 * which], v = edges[4 * pair + 2 * which + 1];
         if (u < 0 || v < 0) continue;
+        if (u >= n || v >= n) {
+            atomicExch(dev_err, DEV_BAD_INPUT);
+            continue;
+        }
         const float g = which ? gd[pair] : gb[pair];
         if (g == 0.0f) continue;
         float acc = 0.0f;
@@ -41,12 +48,12 @@ __global__ void k_backward(const float* __restrict__ pts, int dim, const int32_t
     }
 }
 
-void launch_backward(const float* pts, int dim, const int32_t* edges, int64_t num, const float* gb, const float* gd,
-                     float* grad, cudaStream_t s) {
+void launch_backward(const float* pts, int64_t n, int dim, const int32_t* edges, int64_t num, const float* gb,
+                     const float* gd, float* grad, int* dev_err, cudaStream_t s) {
     if (num <= 0) return;
     int64_t blocks = (2 * num + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
-    k_backward<<<(unsigned)blocks, 256, 0, s>>>(pts, dim, edges, num, gb, gd, grad);
+    k_backward<<<(unsigned)blocks, 256, 0, s>>>(pts, n, dim, edges, num, gb, gd, grad, dev_err);
     VR_CUDA(cudaGetLastError());
 }
 
@@ -56,10 +63,16 @@ extern "C" vr_status vr_backward(const float* pts, int64_t n, int32_t ambient_di
                                  const float* grad_birth, const float* grad_death, float* grad_pts, void* stream) {
     if (n < 1 || ambient_dim < 1 || num < 0 || (num > 0 && (!pts || !edges || !grad_birth || !grad_death || !grad_pts)))
         return VR_ERR_INVALID_ARG;
+    if (num == 0) return VR_OK;
     try {
-        vr::launch_backward(pts, ambient_dim, edges, num, grad_birth, grad_death, grad_pts, (cudaStream_t)stream);
-        VR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-        return VR_OK;
+        cudaStream_t s = (cudaStream_t)stream;
+        vr::Workspace ws(s);
+        int* dev_err = ws.zeros_n<int>(1);
+        vr::launch_backward(pts, n, ambient_dim, edges, num, grad_birth, grad_death, grad_pts, dev_err, s);
+        int h = 0;
+        VR_CUDA(cudaMemcpyAsync(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaStreamSynchronize(s));
+        return h == vr::DEV_OK ? VR_OK : VR_ERR_INVALID_ARG;
     } catch (const vr::Error& e) {
         return e.code;
     }

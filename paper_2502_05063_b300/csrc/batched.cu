@@ -858,7 +858,7 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
     if (!out) return VR_ERR_INVALID_ARG;
     *out = nullptr;
     if (num_clouds < 0 || !offsets || (num_clouds > 0 && !pts) || ambient_dim < 1 || ambient_dim > BMAXDIM ||
-        dmax < 0 || dmax > 1 || std::isnan(threshold) || (flags & ~(uint32_t)VR_CRITICAL_EDGES))
+        dmax < 0 || dmax > 1 || std::isnan(threshold) || (flags & ~(uint32_t)(VR_CRITICAL_EDGES | VR_DEBUG_CHECKS)))
         return VR_ERR_INVALID_ARG;
     if (offsets[0] != 0) return VR_ERR_INVALID_ARG;
     int64_t total = 0, sumsq = 0;
@@ -1051,6 +1051,26 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
         }
         for (auto r : redo) vr_result_free(r);
         (void)sumsq;
+        if (flags & VR_DEBUG_CHECKS) {
+            // per cloud: n_i - 1 finite H0 pairs at most, one essential H0 class at least,
+            // birth <= death, and the documented order within the cloud
+            for (int p = 0; p <= dmax; ++p)
+                for (int i = 0; i < num_clouds; ++i) {
+                    const int64_t a0 = res->pair_offsets[p][i], a1 = res->pair_offsets[p][i + 1];
+                    int64_t ess = 0;
+                    for (int64_t k = a0; k < a1; ++k) {
+                        const vr_pair& x = res->pairs[p][k];
+                        VR_CHECK(x.birth <= x.death && x.birth >= 0.0f, VR_ERR_INTERNAL);
+                        ess += x.death_simplex < 0;
+                        if (k > a0) {
+                            const vr_pair& y = res->pairs[p][k - 1];
+                            VR_CHECK(y.birth < x.birth || (y.birth == x.birth && (y.death < x.death ||
+                                     (y.death == x.death && y.birth_simplex <= x.birth_simplex))), VR_ERR_INTERNAL);
+                        }
+                    }
+                    if (p == 0) VR_CHECK(ess >= 1 && a1 - a0 <= offsets[i + 1] - offsets[i], VR_ERR_INTERNAL);
+                }
+        }
         *out = res;
         return VR_OK;
     } catch (const Error& e) {

@@ -25,6 +25,7 @@ VR_MAX_DIM = 6
 VR_BATCH_MAX_N = 256
 VR_KEEP_ZERO_LENGTH = 0x1
 VR_CRITICAL_EDGES = 0x2
+VR_DEBUG_CHECKS = 0x4
 
 STATUS = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_OOM", 3: "VR_ERR_INDEX_OVERFLOW",
           4: "VR_ERR_CUDA", 5: "VR_ERR_TIMEOUT", 6: "VR_ERR_INTERNAL"}
@@ -85,6 +86,7 @@ lib.vr_sort_u64.argtypes = [_vp, _vp, _i64, _i32, _vp]
 lib.vr_sort_u64_noalloc.argtypes = [_vp, _vp, _i64, _i32, _vp]
 VR_SORT_NOALLOC_MAX_KEYS = 1 << 18
 lib.vr_backward.argtypes = [_vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp]
+lib.vr_probe_read_gbs.argtypes = [_i64, _i32, _vp, ctypes.POINTER(ctypes.c_double)]
 if hasattr(lib, "vr_barcodes_batched"):
     lib.vr_barcodes_batched.argtypes = [_vp, _vp, _i32, _i32, _i32, _f32, _u32, _vp,
                                         ctypes.POINTER(ctypes.POINTER(BatchResult))]
@@ -246,3 +248,11 @@ def backward(pts_dev, edges_dev, grad_birth_dev, grad_death_dev, grad_pts_dev, s
     _check(lib.vr_backward(pts_dev.data_ptr(), int(pts_dev.shape[0]), int(pts_dev.shape[1]), edges_dev.data_ptr(),
                            int(edges_dev.shape[0]), grad_birth_dev.data_ptr(), grad_death_dev.data_ptr(),
                            grad_pts_dev.data_ptr(), _stream_ptr(stream)), "vr_backward")
+
+
+def probe_read_gbs(nbytes: int, iters: int, stream=None) -> float:
+    """Read bandwidth (GB/s) of a device buffer of nbytes, streamed iters times."""
+    out = ctypes.c_double()
+    _check(lib.vr_probe_read_gbs(int(nbytes), int(iters), _stream_ptr(stream), ctypes.byref(out)),
+           "vr_probe_read_gbs")
+    return out.value

@@ -67,6 +67,22 @@ def test_argument_checks_before_cuda(vr):
     assert vr.lib.vr_sort_u64_noalloc(None, None, vr.VR_SORT_NOALLOC_MAX_KEYS + 1, 64, None) == 1
     assert vr.lib.vr_sort_u64(None, None, -1, 64, None) == 1
     assert vr.lib.vr_backward(None, 0, 3, None, 0, None, None, None, None) == 1
+    # VR_DEBUG_CHECKS is a known flag: the call gets past the flag check (and then
+    # fails on the size, before any CUDA call)
+    assert vr.lib.vr_barcodes_points(p, 0, 3, 1, 1.0, vr.VR_DEBUG_CHECKS, None, ctypes.byref(out)) == 1
+
+
+@pytest.mark.parametrize("n,dmax", [(65536, 6), (40000, 5), (65536, 4)])
+def test_index_overflow_before_cuda(vr, n, dmax):
+    """C(n, dmax+2) >= 2^63: the simplex indices of dimension dmax+1 do not fit,
+    reported as VR_ERR_INDEX_OVERFLOW before any device work (no GPU needed)."""
+    assert math.comb(n, dmax + 2) >= 2 ** 63
+    out = ctypes.POINTER(vr.Result)()
+    dummy = np.zeros(3, np.float32)  # never read: the check comes first
+    assert vr.lib.vr_barcodes_points(dummy.ctypes.data, n, 3, dmax, float("inf"), 0, None,
+                                     ctypes.byref(out)) == 3
+    assert vr.lib.vr_barcodes_dists(dummy.ctypes.data, n, dmax, 1.0, 0, None, ctypes.byref(out)) == 3
+    assert not out
 
 
 def test_product_path_has_no_oracle_dependency():

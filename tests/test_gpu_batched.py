@@ -60,25 +60,25 @@ def test_batched_equals_single(vr, dmax, thr, flags):
 
 def test_batch4096_workload(vr):
     """The full 4096-cloud workload: every cloud equals the single-cloud path,
-    every 64th cloud equals the oracle."""
+    and every 8th cloud (512 clouds, all three kinds, sizes 32..256) equals the
+    oracle, which runs one cloud per process on the host cores."""
     import torch
+    from oracle import pool
     clouds, kinds = synth.batch_clouds()
     pts, offs = synth.pack(clouds)
     bb = vr.barcodes_batched(torch.from_numpy(pts).cuda(), offs, dmax=1)
-    for i in range(0, len(clouds), 64):
-        c = clouds[i]
-        n = c.shape[0]
-        D = oracle.distances_f32(c).astype(np.float64)
-        pairs, _ = oracle.cohom(D, n, 1, oracle.enclosing_radius(D, n), clearing=True)
-        dg = oracle.diagram(pairs, 1)
+    sample = list(range(0, len(clouds), 8))
+    dgs = pool.diagrams([clouds[i] for i in sample], 1)
+    for i, dg in zip(sample, dgs):
         for p in range(2):
             want = [(float(np.float32(r["birth"])), float(np.float32(r["death"])) if np.isfinite(r["death"]) else math.inf,
                      int(r["birth_cidx"]), int(r["death_cidx"])) for r in dg[p]]
             assert rows(bb.cloud(i, p)) == want, (i, p, kinds[i])
-    for i in range(1, len(clouds), 7):
+    for i in range(len(clouds)):
         single = vr.barcodes(points=clouds[i], dmax=1)
         for p in range(2):
             assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
+        assert bb.thresholds[i] == np.float32(single.threshold), i
 
 
 def test_batched_repeat_and_shapes(vr):
