@@ -120,7 +120,8 @@ __device__ __forceinline__ void decode_simplex(const Binom& B, uint64_t c, int64
 // root.  C(x, k) and C(x+1, k) are read together, so an exact estimate costs
 // one table round trip; otherwise a few checked steps correct it.  Returns
 // false if they run out (the caller then searches); *cv receives C(v, k).
-__device__ __forceinline__ bool binom_root(const Binom& B, uint64_t c, int k, int64_t lo, int64_t hi, int64_t& v,
+template <class BT = Binom>
+__device__ __forceinline__ bool binom_root(const BT& B, uint64_t c, int k, int64_t lo, int64_t hi, int64_t& v,
                                            uint64_t& cv) {
     if (k == 1) {  // C(v,1) = v
         v = c < (uint64_t)hi ? (int64_t)c : hi;
@@ -159,15 +160,15 @@ __device__ __forceinline__ bool binom_root(const Binom& B, uint64_t c, int k, in
 // search (lane L tests lo + L * step; the tested values C(x, k) grow with
 // x, so the passing lanes form a prefix), two dependent table reads per
 // vertex for n <= 1024.  Every lane computes and receives the same v.
-template <int Q>
-__device__ __forceinline__ void warp_decode_simplex(const Binom& B, uint64_t c, int64_t top, int* v) {
+template <int Q, class BT = Binom>
+__device__ __forceinline__ void warp_decode_simplex(const BT& B, uint64_t c, int64_t top, int* v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = Q; i >= 0; --i) {
         int64_t lo = i, hi = top;  // C(lo, i+1) <= c holds throughout
         int64_t r;
         uint64_t cr;
-        if (i + 1 <= 4 && binom_root(B, c, i + 1, lo, hi, r, cr)) {
+        if (i + 1 <= 4 && binom_root<BT>(B, c, i + 1, lo, hi, r, cr)) {
             v[i] = (int)r;
             c -= cr;
             top = r - 1;
