@@ -247,6 +247,52 @@ def other_workload_rates(stream, reps=5):
     return out
 
 
+RANDPERM_NS = (50, 100, 200, 400, 1000, 2000, 4000, 9000)
+
+
+def randperm_curve(stream):
+    """The apparent-fraction experiment (Sec. 5.6.6, Fig 5.14): distance matrices
+    whose lower triangle is a random permutation of 1..n(n-1)/2, the full
+    2-skeleton, dimension 1.  Per n: the apparent fraction (mean, min, max over
+    the samples) beside the Thm 5.4.2 bound (n-2)/n, and the rate of the fused
+    filtration/apparent kernel (library stage timer) and of the whole
+    apparent-only call (CUDA events; device-resident input)."""
+    import numpy as np
+    import torch
+    from paper_2502_05063_b300 import synth, vr
+    out = {}
+    for n in RANDPERM_NS:
+        samples = 10 if n <= 1000 else 3
+        m = n * (n - 1) // 2
+        fr, kms, cms, cof = [], [], [], []
+        for smp in range(samples):
+            D = synth.random_permutation_dists(n, sample=smp)
+            d = torch.from_numpy(D).cuda()
+            thr = float(D.max())
+            flags = vr.VR_APPARENT_ONLY
+            vr.barcodes(dists=d, n=n, dmax=1, threshold=thr, flags=flags, stream=stream)  # warm
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bc = vr.barcodes(dists=d, n=n, dmax=1, threshold=thr, flags=flags, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            st = bc.stats[1]
+            fr.append(st["apparent"] / m)
+            kms.append(st["ms_filtration"])
+            cms.append(e0.elapsed_time(e1))
+            cof.append(st["cofacets_scanned"])
+        k = statistics.median(kms)
+        out[str(n)] = {"samples": samples, "apparent_fraction_mean": statistics.mean(fr),
+                       "apparent_fraction_min": min(fr), "apparent_fraction_max": max(fr),
+                       "upper_bound": (n - 2) / n, "kernel_ms": k,
+                       "kernel_simplices_per_s": m / (k / 1e3) if k > 0 else None,
+                       "kernel_cofacets_per_s": statistics.median(cof) / (k / 1e3) if k > 0 else None,
+                       "call_ms": statistics.median(cms), "call_simplices_per_s": m / (statistics.median(cms) / 1e3)}
+    return {"curve": out, "workload": "random permutation of 1..n(n-1)/2 as the lower triangle (ordered distinct "
+                                      "floats), full 2-skeleton, H0 and the dimension-1 apparent search "
+                                      "(VR_APPARENT_ONLY), seed 5, sample s from stream (5, n, s)"}
+
+
 def probe_peaks(stream):
     """Project-written read probes (vr_probe_read_gbs): L2-resident and HBM."""
     from paper_2502_05063_b300 import vr
@@ -503,6 +549,7 @@ def run_ours(args):
     if not args.no_batched:
         line["batched"] = batched_metrics(stream)
         line["other_workloads"] = other_workload_rates(stream)
+        line["randperm"] = randperm_curve(stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_single()
         if not args.no_batched:

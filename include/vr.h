@@ -66,6 +66,13 @@ typedef enum {
                                     columns = death simplices one dimension down; birth <=
                                     death; documented pair order); a violation returns
                                     VR_ERR_INTERNAL.  Host-side, after the computation.     */
+#define VR_APPARENT_ONLY    0x8u /* top dimension dmax: stop after filtration with clearing and
+                                    the apparent-pair search (the quantity of the apparent-
+                                    fraction experiment, Sec. 5.6.6): stats[dmax] is filled up
+                                    to `reduced` (its non-apparent columns, not reduced),
+                                    stats[dmax].pairs counts the apparent pairs, and no pairs
+                                    of dimension dmax are returned (count[dmax] = 0).
+                                    Dimensions below dmax are computed in full.              */
 
 /* One persistence pair of dimension p.  birth = diam(birth simplex),
  * death = diam(death simplex) or +INFINITY for an essential class. */

@@ -284,9 +284,15 @@ static void fill_dim(vr_result* res, int p, const HostPairs& hp, const std::vect
 // the cleared ones are exactly the death simplices of the (p-1)-pairs
 // (Sec. 5.2.3), and every kept column is paired or essential.  Each emitted
 // pair has birth <= death, and the pairs are sorted as documented.
-static void debug_checks(const vr_result* res) {
+static void debug_checks(const vr_result* res, uint32_t flags) {
     for (int p = 0; p <= res->dmax; ++p) {
         const vr_stats& st = res->stats[p];
+        if ((flags & VR_APPARENT_ONLY) && p == res->dmax && p >= 1) {  // no reduction in this dimension
+            VR_CHECK(st.reduced + st.apparent == st.columns && res->count[p] == 0, VR_ERR_INTERNAL);
+            VR_CHECK(st.cleared == res->stats[p - 1].pairs, VR_ERR_INTERNAL);
+            VR_CHECK(st.candidates == st.above_threshold + st.cleared + st.columns, VR_ERR_INTERNAL);
+            continue;
+        }
         VR_CHECK(st.columns == st.pairs + st.essential, VR_ERR_INTERNAL);
         if (p >= 1) {
             VR_CHECK(st.cleared == res->stats[p - 1].pairs, VR_ERR_INTERNAL);
@@ -430,6 +436,23 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         // p+1 per examined cofacet, all pairs of t for each facet test
         st.lookups = (int64_t)ncand * (p + 1) * p / 2 + hs.p[6] * (p + 1) + hs.p[7] * (p + 2) * (p + 1) / 2;
         st.cofacets_scanned = hs.p[6];
+        if ((flags & VR_APPARENT_ONLY) && p == dmax) {
+            // the top dimension stops after the apparent-pair search: its apparent
+            // pairs are counted, its non-apparent columns are not reduced
+            st.pairs = st.apparent;
+            res->pairs[p] = (vr_pair*)malloc(sizeof(vr_pair));
+            if (!res->pairs[p]) throw Error{VR_ERR_OOM};
+            if (want_edges) {
+                res->critical_edges[p] = (int32_t*)malloc(4 * sizeof(int32_t));
+                if (!res->critical_edges[p]) throw Error{VR_ERR_OOM};
+            }
+            res->count[p] = 0;
+            log.mark(stage_name("launch sort", p));
+            log.mark(stage_name("sort", p));
+            log.mark(stage_name("launch reduce", p));
+            log.mark(stage_name("reduce", p));
+            break;
+        }
         log.mark(stage_name("launch sort", p));
         radix_sort_u64(ws, keys, nullptr, nna, rank_bits + cb);
         log.mark(stage_name("sort", p));
@@ -478,7 +501,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         res->stats[p].ms_reduce = log.between(stage_name("launch reduce", p), stage_name("reduce", p));
     }
     if (log_enabled()) log.print();
-    if (flags & VR_DEBUG_CHECKS) debug_checks(res);
+    if (flags & VR_DEBUG_CHECKS) debug_checks(res, flags);
     guard.r = nullptr;
     return res;
 }
@@ -490,7 +513,8 @@ static vr_status run_guarded(vr_result** out, const float* data, bool is_points,
     if (!data && n > 1) return VR_ERR_INVALID_ARG;
     if (n < 1 || n > (1 << 16) || dmax < 0 || dmax > VR_MAX_DIM || std::isnan(threshold)) return VR_ERR_INVALID_ARG;
     if (is_points && (amb < 1 || amb > 1024)) return VR_ERR_INVALID_ARG;
-    if (flags & ~(uint32_t)(VR_KEEP_ZERO_LENGTH | VR_CRITICAL_EDGES | VR_DEBUG_CHECKS)) return VR_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)(VR_KEEP_ZERO_LENGTH | VR_CRITICAL_EDGES | VR_DEBUG_CHECKS | VR_APPARENT_ONLY))
+        return VR_ERR_INVALID_ARG;
     // simplex indices of dimension dmax+1 must fit 63 bits (checked before any device work)
     if (binom_host(n, dmax + 2) >= (1ull << 63)) return VR_ERR_INDEX_OVERFLOW;
     try {

@@ -18,6 +18,9 @@ Workloads (name -> generator, homology dims, threshold):
                z=0 plane, 3-D noise), noisy sphere S^2 (same radius law and noise) or uniform
                in [0,1]^3 with probability 1/3 each, seed 3, cloud i from stream (3, i), H0-H1
   circles256   256 clouds of n=128 on the unit circle in R^2 + N(0, 0.1^2), seed 4, H0-H1
+  randperm     distance matrices whose lower triangle is a random permutation of
+               1 .. n(n-1)/2 (stored as ordered distinct floats), n = 50 .. 9000,
+               seed 5, sample s from stream (5, n, s), H0-H1 of the full 2-skeleton
 """
 from __future__ import annotations
 
@@ -91,6 +94,18 @@ def batch_clouds(num: int = 4096, nmin: int = 32, nmax: int = 256, seed: int = 3
 
 def circles(num: int = 256, n: int = 128, sigma: float = 0.1, seed: int = 4):
     return [circle(n, 1.0, sigma, 2, g=_rng(seed, i)) for i in range(num)]
+
+
+def random_permutation_dists(n: int, seed: int = 5, sample: int = 0) -> np.ndarray:
+    """Condensed lower triangle whose entries are a uniformly random permutation
+    of 1 .. n(n-1)/2 (the random distance matrices of the apparent-fraction
+    experiment, Sec. 5.6.6), stored as float32.  Only the order of the
+    entries matters (Obs 5.6.8) and integers past 2^24 are not all float32
+    values, so rank k is stored as the k-th float32 above 1.0 (bit pattern of
+    1.0 plus k): distinct, finite and in the same order."""
+    m = n * (n - 1) // 2
+    perm = _rng(seed, n, sample).permutation(m).astype(np.uint32) + np.uint32(1)
+    return (perm + np.uint32(0x3F800000)).view(np.float32)
 
 
 def pack(clouds):

@@ -26,6 +26,7 @@ VR_BATCH_MAX_N = 256
 VR_KEEP_ZERO_LENGTH = 0x1
 VR_CRITICAL_EDGES = 0x2
 VR_DEBUG_CHECKS = 0x4
+VR_APPARENT_ONLY = 0x8
 
 STATUS = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_OOM", 3: "VR_ERR_INDEX_OVERFLOW",
           4: "VR_ERR_CUDA", 5: "VR_ERR_TIMEOUT", 6: "VR_ERR_INTERNAL"}
