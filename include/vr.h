@@ -141,6 +141,29 @@ vr_status vr_barcodes_dists(const float* lower_tri, int64_t n, int32_t dmax, flo
 
 void vr_result_free(vr_result* r);
 
+/* Device-resident variants (for callers that keep the pairs on the GPU, such
+ * as the torch autograd path): the same computation and the same pairs, in
+ * the same order, but pairs[p] and critical_edges[p] are DEVICE pointers on
+ * the call's device, allocated by the library (cudaMalloc) and released by
+ * vr_device_result_free; counts, stats and the threshold are on the host.
+ * The pairs are ordered and filtered on the device; nothing but counts goes
+ * to the host.  Arguments and errors as vr_barcodes_points / _dists. */
+typedef struct {
+    int32_t dmax;
+    int64_t n;
+    float threshold;
+    int64_t count[VR_MAX_DIM + 1];
+    vr_pair* pairs[VR_MAX_DIM + 1];            /* device, count[p] entries (at least one allocated) */
+    int32_t* critical_edges[VR_MAX_DIM + 1];   /* device, 4 per pair, if VR_CRITICAL_EDGES; else NULL */
+    vr_stats stats[VR_MAX_DIM + 1];
+} vr_device_result;
+
+vr_status vr_barcodes_points_device(const float* pts, int64_t n, int32_t ambient_dim, int32_t dmax,
+                                    float threshold, uint32_t flags, void* stream, vr_device_result** out);
+vr_status vr_barcodes_dists_device(const float* lower_tri, int64_t n, int32_t dmax, float threshold,
+                                   uint32_t flags, void* stream, vr_device_result** out);
+void vr_device_result_free(vr_device_result* r);
+
 /* Batched barcodes of many independent clouds (the batched form: one
  * persistent launch over a work queue of clouds).
  *  pts        float[sum n_i][ambient_dim], clouds stored back to back, host or device.
@@ -163,6 +186,24 @@ vr_status vr_barcodes_batched(const float* pts, const int64_t* offsets, int32_t 
                               int32_t ambient_dim, int32_t dmax, float threshold, uint32_t flags,
                               void* stream, vr_batch_result** out);
 void vr_batch_result_free(vr_batch_result* r);
+
+/* Device-resident variant of vr_barcodes_batched: the same pairs in the same
+ * order; pairs[p] and critical_edges[p] are device pointers (cudaMalloc by
+ * the library), pair_offsets and thresholds host arrays, all released by
+ * vr_batch_device_result_free. */
+typedef struct {
+    int32_t num_clouds;
+    int32_t dmax;
+    int64_t* pair_offsets[2];           /* host, int64[num_clouds+1] per dimension        */
+    vr_pair* pairs[2];                  /* device                                          */
+    int32_t* critical_edges[2];         /* device, 4 per pair if VR_CRITICAL_EDGES, else NULL */
+    float* thresholds;                  /* host, float[num_clouds]                          */
+} vr_batch_device_result;
+
+vr_status vr_barcodes_batched_device(const float* pts, const int64_t* offsets, int32_t num_clouds,
+                                     int32_t ambient_dim, int32_t dmax, float threshold, uint32_t flags,
+                                     void* stream, vr_batch_device_result** out);
+void vr_batch_device_result_free(vr_batch_device_result* r);
 
 /* Backward pass: d loss / d pts given d loss / d (birth, death) of the pairs
  * of a forward result computed with VR_CRITICAL_EDGES.  Each finite value is

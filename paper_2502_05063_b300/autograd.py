@@ -1,7 +1,8 @@
 """Differentiable persistence diagrams (torch.autograd.Function).
 
 Forward: the CUDA library computes the pairs and, for each finite birth and
-death, the critical edge (u, v) whose length it is.  Backward: the library's
+death, the critical edge (u, v) whose length it is, and leaves both on the
+GPU (the device-resident entry points).  Backward: the library's
 backward kernel scatters dL/d(birth, death) through those edges onto the
 point coordinates (d|x_u - x_v| / dx_u = (x_u - x_v) / |x_u - x_v|).  The
 pairing is piecewise constant in the coordinates, so this is the gradient
@@ -19,7 +20,9 @@ from . import vr
 
 
 def _edges_tensor(bc, dmax, device):
-    parts = [torch.from_numpy(bc.critical_edges[p].astype(np.int32)) for p in range(dmax + 1)]
+    """Critical edges of every dimension, concatenated (device tensors from the
+    device-resident result: no host round trip)."""
+    parts = [bc.edges[p] for p in range(dmax + 1)]
     return torch.cat(parts).to(device) if parts else torch.zeros((0, 4), dtype=torch.int32, device=device)
 
 
@@ -32,14 +35,10 @@ class VRDiagram(torch.autograd.Function):
     def forward(ctx, points, dmax, threshold=float("inf"), recompute=False):
         x = points.detach().contiguous()
         stream = torch.cuda.current_stream(x.device)
-        bc = vr.barcodes(points=x, dmax=dmax, threshold=threshold, flags=vr.VR_CRITICAL_EDGES, stream=stream)
-        outs = []
-        for p in range(dmax + 1):
-            a = bc.pairs[p]
-            t = torch.from_numpy(np.stack([a["birth"], a["death"]], 1).astype(np.float32)).to(x.device)
-            outs.append(t)
+        bc = vr.barcodes_device(points=x, dmax=dmax, threshold=threshold, flags=vr.VR_CRITICAL_EDGES, stream=stream)
+        outs = [bc.values[p] for p in range(dmax + 1)]
         ctx.dmax, ctx.threshold, ctx.recompute = dmax, threshold, recompute
-        ctx.counts = [len(bc.pairs[p]) for p in range(dmax + 1)]
+        ctx.counts = list(bc.counts)
         if recompute:
             ctx.save_for_backward(points)
         else:
@@ -51,8 +50,8 @@ class VRDiagram(torch.autograd.Function):
         if ctx.recompute:
             (points,) = ctx.saved_tensors
             x = points.detach().contiguous()
-            bc = vr.barcodes(points=x, dmax=ctx.dmax, threshold=ctx.threshold, flags=vr.VR_CRITICAL_EDGES,
-                             stream=torch.cuda.current_stream(x.device))
+            bc = vr.barcodes_device(points=x, dmax=ctx.dmax, threshold=ctx.threshold, flags=vr.VR_CRITICAL_EDGES,
+                                    stream=torch.cuda.current_stream(x.device))
             edges = _edges_tensor(bc, ctx.dmax, x.device)
         else:
             points, edges = ctx.saved_tensors
@@ -84,15 +83,12 @@ class VRDiagramBatched(torch.autograd.Function):
         x = points.detach().contiguous()
         offs = np.ascontiguousarray(offsets, dtype=np.int64)
         stream = torch.cuda.current_stream(x.device)
-        bb = vr.barcodes_batched(x, offs, dmax=dmax, threshold=threshold, flags=vr.VR_CRITICAL_EDGES, stream=stream)
-        outs, offs_out, edges = [], [], []
-        for p in range(dmax + 1):
-            a = bb.pairs[p]
-            outs.append(torch.from_numpy(np.stack([a["birth"], a["death"]], 1).astype(np.float32)).to(x.device))
-            offs_out.append(torch.from_numpy(bb.offsets[p].astype(np.int64)))
-            edges.append(torch.from_numpy(bb.critical_edges[p].astype(np.int32)))
-        ctx.counts = [len(bb.pairs[p]) for p in range(dmax + 1)]
-        ctx.save_for_backward(points, torch.cat(edges).to(x.device))
+        bb = vr.barcodes_batched_device(x, offs, dmax=dmax, threshold=threshold, flags=vr.VR_CRITICAL_EDGES,
+                                        stream=stream)
+        outs = [bb.values[p] for p in range(dmax + 1)]
+        offs_out = [torch.from_numpy(bb.offsets[p].astype(np.int64)) for p in range(dmax + 1)]
+        ctx.counts = [int(bb.offsets[p][-1]) for p in range(dmax + 1)]
+        ctx.save_for_backward(points, torch.cat([bb.edges[p] for p in range(dmax + 1)]))
         for o in offs_out:
             ctx.mark_non_differentiable(o)
         return tuple(outs) + tuple(offs_out)

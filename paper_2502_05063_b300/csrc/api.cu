@@ -193,6 +193,87 @@ static HostPairs fetch_pairs(Workspace& ws, const PairRec* dev, int64_t num, int
 }
 
 // ---------------------------------------------------------------------------
+// device-resident output: filter, order and convert the records on the device
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool dropped(const PairRec& r, int keep_zero) {
+    return !keep_zero && r.death_rank != 0xFFFFFFFFu && r.death_rank == r.birth_rank;
+}
+
+__global__ void k_emit_keys1(const PairRec* __restrict__ recs, int64_t num, int keep_zero, uint64_t* __restrict__ keys,
+                             uint64_t* __restrict__ idx, unsigned long long* __restrict__ kept) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < num; k += (int64_t)gridDim.x * blockDim.x) {
+        const PairRec r = recs[k];
+        keys[k] = r.birth_cidx;
+        idx[k] = (uint64_t)k;
+        if (!dropped(r, keep_zero)) atomicAdd(kept, 1ull);
+    }
+}
+
+// second (stable) pass: birth rank, then death rank; dropped records last
+__global__ void k_emit_keys2(const PairRec* __restrict__ recs, int64_t num, int keep_zero,
+                             const uint64_t* __restrict__ idx, uint64_t* __restrict__ keys) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < num; k += (int64_t)gridDim.x * blockDim.x) {
+        const PairRec r = recs[idx[k]];
+        keys[k] = dropped(r, keep_zero) ? ~0ull : (((uint64_t)r.birth_rank << 32) | r.death_rank);
+    }
+}
+
+__global__ void k_emit_gather(const PairRec* __restrict__ recs, int64_t cnt, const uint64_t* __restrict__ idx,
+                              const float* __restrict__ values, PairRec* __restrict__ sorted,
+                              vr_pair* __restrict__ out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += (int64_t)gridDim.x * blockDim.x) {
+        const PairRec r = recs[idx[k]];
+        sorted[k] = r;
+        vr_pair v;
+        v.birth = values[r.birth_rank];
+        v.death = r.death_rank == 0xFFFFFFFFu ? __int_as_float(0x7f800000) : values[r.death_rank];
+        v.birth_simplex = r.birth_cidx;
+        v.death_simplex = r.death_cidx;
+        out[k] = v;
+    }
+}
+
+// Pairs of dimension p as the host path would return them (zero-length ones
+// dropped unless keep_zero; sorted by (birth, death, birth simplex)), in
+// device memory that outlives the call (cudaMalloc; vr_device_result_free).
+static int64_t device_emit(Workspace& ws, HostScratch& hs, const PairRec* recs, int64_t num, int p,
+                           const RankMatrix& R, const Binom& B, const float* values, bool keep_zero,
+                           bool want_edges, vr_pair** out, int32_t** edges) {
+    cudaStream_t s = ws.stream;
+    int64_t cnt = 0;
+    if (num > 0) {
+        uint64_t* keys = ws.alloc_n<uint64_t>(num);
+        uint64_t* idx = ws.alloc_n<uint64_t>(num);
+        unsigned long long* kept = ws.zeros_n<unsigned long long>(1);
+        const unsigned blocks = (unsigned)std::min<int64_t>((num + 255) / 256, 4096);
+        k_emit_keys1<<<blocks, 256, 0, s>>>(recs, num, keep_zero ? 1 : 0, keys, idx, kept);
+        VR_CUDA(cudaGetLastError());
+        radix_sort_u64(ws, keys, idx, num, 64);
+        k_emit_keys2<<<blocks, 256, 0, s>>>(recs, num, keep_zero ? 1 : 0, idx, keys);
+        VR_CUDA(cudaGetLastError());
+        radix_sort_u64(ws, keys, idx, num, 64);
+        VR_CUDA(cudaMemcpyAsync(&hs.p[40], kept, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaStreamSynchronize(s));
+        cnt = hs.p[40];
+        VR_CUDA(cudaMalloc(out, (size_t)std::max<int64_t>(cnt, 1) * sizeof(vr_pair)));
+        if (want_edges) VR_CUDA(cudaMalloc(edges, (size_t)std::max<int64_t>(cnt, 1) * 4 * sizeof(int32_t)));
+        if (cnt > 0) {
+            PairRec* sorted = ws.alloc_n<PairRec>(cnt);
+            k_emit_gather<<<blocks, 256, 0, s>>>(recs, cnt, idx, values, sorted, *out);
+            VR_CUDA(cudaGetLastError());
+            if (want_edges) {
+                k_critical_edges<<<blocks, 128, 0, s>>>(sorted, cnt, p, R, B, *edges);
+                VR_CUDA(cudaGetLastError());
+            }
+        }
+    } else {
+        VR_CUDA(cudaMalloc(out, sizeof(vr_pair)));
+        if (want_edges) VR_CUDA(cudaMalloc(edges, 4 * sizeof(int32_t)));
+    }
+    return cnt;
+}
+
+// ---------------------------------------------------------------------------
 // optional stage log (VR_LOG=1): CUDA-event time of each stage on the stream
 // ---------------------------------------------------------------------------
 bool log_enabled() {
@@ -299,7 +380,7 @@ static void debug_checks(const vr_result* res, uint32_t flags) {
             VR_CHECK(st.candidates == st.above_threshold + st.cleared + st.columns, VR_ERR_INTERNAL);
             VR_CHECK(st.reduced + st.apparent <= st.columns, VR_ERR_INTERNAL);
         }
-        for (int64_t k = 0; k < res->count[p]; ++k) {
+        for (int64_t k = 0; res->pairs[p] && k < res->count[p]; ++k) {  // host results only
             const vr_pair& a = res->pairs[p][k];
             VR_CHECK(a.birth <= a.death && a.birth >= 0.0f, VR_ERR_INTERNAL);
             VR_CHECK((a.death_simplex < 0) == std::isinf(a.death), VR_ERR_INTERNAL);
@@ -316,7 +397,22 @@ static void debug_checks(const vr_result* res, uint32_t flags) {
 // ---------------------------------------------------------------------------
 // the driver
 // ---------------------------------------------------------------------------
-static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax, float threshold, uint32_t flags) {
+// Device-resident pairs (vr_barcodes_*_device): per dimension, the sorted
+// pairs and critical edges in device memory owned by the caller's result.
+struct DevOut {
+    vr_pair* pairs[VR_MAX_DIM + 1];
+    int32_t* edges[VR_MAX_DIM + 1];
+};
+
+__global__ void k_count_essential(const PairRec* __restrict__ recs, int64_t num, unsigned long long* __restrict__ c) {
+    unsigned long long k = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < num; i += (int64_t)gridDim.x * blockDim.x)
+        k += recs[i].death_rank == 0xFFFFFFFFu;
+    if (k) atomicAdd(c, k);
+}
+
+static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax, float threshold, uint32_t flags,
+                          DevOut* dv = nullptr) {
     HostScratch& hs = host_scratch();
     const bool keep_zero = flags & VR_KEEP_ZERO_LENGTH;
     const bool want_edges = flags & VR_CRITICAL_EDGES;
@@ -376,14 +472,26 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
     VR_CUDA(cudaStreamSynchronize(s));
     {
         const int64_t m0 = (int64_t)(int32_t)(hs.p[0] & 0xFFFFFFFF);
-        HostPairs hp = fetch_pairs(ws, p0, m0, 0, R, B, want_edges);
         int64_t ess = 0;
-        for (auto& r : hp.recs) ess += r.death_rank == 0xFFFFFFFFu;
         res->stats[0].candidates = n;
         res->stats[0].columns = n;
+        if (dv) {
+            unsigned long long* ce = ws.zeros_n<unsigned long long>(1);
+            k_count_essential<<<(unsigned)std::min<int64_t>((m0 + 255) / 256 + 1, 1024), 256, 0, s>>>(p0, m0, ce);
+            VR_CUDA(cudaGetLastError());
+            VR_CUDA(cudaMemcpyAsync(&hs.p[41], ce, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaStreamSynchronize(s));
+            ess = hs.p[41];
+            res->count[0] = device_emit(ws, hs, p0, m0, 0, R, B, ri.values, keep_zero, want_edges, &dv->pairs[0],
+                                        &dv->edges[0]);
+            res->stats[0].emitted = res->count[0];
+        } else {
+            HostPairs hp = fetch_pairs(ws, p0, m0, 0, R, B, want_edges);
+            for (auto& r : hp.recs) ess += r.death_rank == 0xFFFFFFFFu;
+            fill_dim(res, 0, hp, values, keep_zero, want_edges);
+        }
         res->stats[0].pairs = m0 - ess;
         res->stats[0].essential = ess;
-        fill_dim(res, 0, hp, values, keep_zero, want_edges);
     }
 
     // ---- dimensions 1..dmax
@@ -440,11 +548,16 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
             // the top dimension stops after the apparent-pair search: its apparent
             // pairs are counted, its non-apparent columns are not reduced
             st.pairs = st.apparent;
-            res->pairs[p] = (vr_pair*)malloc(sizeof(vr_pair));
-            if (!res->pairs[p]) throw Error{VR_ERR_OOM};
-            if (want_edges) {
-                res->critical_edges[p] = (int32_t*)malloc(4 * sizeof(int32_t));
-                if (!res->critical_edges[p]) throw Error{VR_ERR_OOM};
+            if (dv) {
+                device_emit(ws, hs, nullptr, 0, p, R, B, ri.values, keep_zero, want_edges, &dv->pairs[p],
+                            &dv->edges[p]);
+            } else {
+                res->pairs[p] = (vr_pair*)malloc(sizeof(vr_pair));
+                if (!res->pairs[p]) throw Error{VR_ERR_OOM};
+                if (want_edges) {
+                    res->critical_edges[p] = (int32_t*)malloc(4 * sizeof(int32_t));
+                    if (!res->critical_edges[p]) throw Error{VR_ERR_OOM};
+                }
             }
             res->count[p] = 0;
             log.mark(stage_name("launch sort", p));
@@ -482,13 +595,28 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         st.additions = hs.p[9];
         st.pairs = hs.p[10] + st.apparent;
         st.essential = hs.p[11];
-        HostPairs hp = fetch_pairs(ws, pr, hs.p[8], p, R, B, want_edges);
-        if (keep_zero && nzero > 0) {
-            HostPairs hz = fetch_pairs(ws, zero_pairs, nzero, p, R, B, want_edges);
-            hp.recs.insert(hp.recs.end(), hz.recs.begin(), hz.recs.end());
-            hp.edges.insert(hp.edges.end(), hz.edges.begin(), hz.edges.end());
+        if (dv) {
+            const PairRec* src = pr;
+            int64_t num = hs.p[8];
+            if (keep_zero && nzero > 0) {  // the reduction's pairs, then the apparent ones
+                PairRec* cat = ws.alloc_n<PairRec>(num + nzero);
+                VR_CUDA(cudaMemcpyAsync(cat, pr, num * sizeof(PairRec), cudaMemcpyDeviceToDevice, s));
+                VR_CUDA(cudaMemcpyAsync(cat + num, zero_pairs, nzero * sizeof(PairRec), cudaMemcpyDeviceToDevice, s));
+                src = cat;
+                num += nzero;
+            }
+            res->count[p] = device_emit(ws, hs, src, num, p, R, B, ri.values, keep_zero, want_edges, &dv->pairs[p],
+                                        &dv->edges[p]);
+            st.emitted = res->count[p];
+        } else {
+            HostPairs hp = fetch_pairs(ws, pr, hs.p[8], p, R, B, want_edges);
+            if (keep_zero && nzero > 0) {
+                HostPairs hz = fetch_pairs(ws, zero_pairs, nzero, p, R, B, want_edges);
+                hp.recs.insert(hp.recs.end(), hz.recs.begin(), hz.recs.end());
+                hp.edges.insert(hp.edges.end(), hz.edges.begin(), hz.edges.end());
+            }
+            fill_dim(res, p, hp, values, keep_zero, want_edges);
         }
-        fill_dim(res, p, hp, values, keep_zero, want_edges);
         log.mark(stage_name("emit", p));
         clear = clear_next;
     }
@@ -507,7 +635,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
 }
 
 static vr_status run_guarded(vr_result** out, const float* data, bool is_points, int64_t n, int32_t amb,
-                             int32_t dmax, float threshold, uint32_t flags, void* stream) {
+                             int32_t dmax, float threshold, uint32_t flags, void* stream, DevOut* dv = nullptr) {
     if (!out) return VR_ERR_INVALID_ARG;
     *out = nullptr;
     if (!data && n > 1) return VR_ERR_INVALID_ARG;
@@ -539,7 +667,7 @@ static vr_status run_guarded(vr_result** out, const float* data, bool is_points,
             launch_check_lower_tri(lower, m, err, s);
             check_dev_err(err, s);
         }
-        *out = compute(ws, lower, n, dmax, threshold, flags);
+        *out = compute(ws, lower, n, dmax, threshold, flags, dv);
         VR_CUDA(cudaStreamSynchronize(s));
         return VR_OK;
     } catch (const Error& e) {
@@ -550,6 +678,56 @@ static vr_status run_guarded(vr_result** out, const float* data, bool is_points,
     } catch (...) {
         return VR_ERR_INTERNAL;
     }
+}
+
+static void free_devout(DevOut& dv) {
+    for (int p = 0; p <= VR_MAX_DIM; ++p) {
+        if (dv.pairs[p]) cudaFree(dv.pairs[p]);
+        if (dv.edges[p]) cudaFree(dv.edges[p]);
+        dv.pairs[p] = nullptr;
+        dv.edges[p] = nullptr;
+    }
+}
+
+static vr_status run_device(vr_device_result** out, const float* data, bool is_points, int64_t n, int32_t amb,
+                            int32_t dmax, float threshold, uint32_t flags, void* stream) {
+    if (!out) return VR_ERR_INVALID_ARG;
+    *out = nullptr;
+    DevOut dv;
+    memset(&dv, 0, sizeof dv);
+    vr_result* r = nullptr;
+    vr_status st = run_guarded(&r, data, is_points, n, amb, dmax, threshold, flags, stream, &dv);
+    if (st != VR_OK) {
+        free_devout(dv);
+        return st;
+    }
+    vr_device_result* d = (vr_device_result*)calloc(1, sizeof(vr_device_result));
+    if (!d) {
+        free_devout(dv);
+        vr_result_free(r);
+        return VR_ERR_OOM;
+    }
+    d->dmax = r->dmax;
+    d->n = r->n;
+    d->threshold = r->threshold;
+    memcpy(d->count, r->count, sizeof d->count);
+    memcpy(d->stats, r->stats, sizeof d->stats);
+    vr_result_free(r);
+    const bool want_edges = flags & VR_CRITICAL_EDGES;
+    for (int p = 0; p <= dmax; ++p) {
+        if (!dv.pairs[p] && cudaMalloc(&dv.pairs[p], sizeof(vr_pair)) != cudaSuccess) st = VR_ERR_OOM;
+        if (want_edges && !dv.edges[p] && cudaMalloc(&dv.edges[p], 4 * sizeof(int32_t)) != cudaSuccess)
+            st = VR_ERR_OOM;
+        d->pairs[p] = dv.pairs[p];
+        d->critical_edges[p] = want_edges ? dv.edges[p] : nullptr;
+    }
+    if (st != VR_OK) {
+        free_devout(dv);
+        free(d);
+        return st;
+    }
+    *out = d;
+    return VR_OK;
 }
 
 }  // namespace vr
@@ -567,6 +745,25 @@ vr_status vr_barcodes_points(const float* pts, int64_t n, int32_t ambient_dim, i
 vr_status vr_barcodes_dists(const float* lower_tri, int64_t n, int32_t dmax, float threshold, uint32_t flags,
                             void* stream, vr_result** out) {
     return vr::run_guarded(out, lower_tri, false, n, 0, dmax, threshold, flags, stream);
+}
+
+vr_status vr_barcodes_points_device(const float* pts, int64_t n, int32_t ambient_dim, int32_t dmax, float threshold,
+                                    uint32_t flags, void* stream, vr_device_result** out) {
+    return vr::run_device(out, pts, true, n, ambient_dim, dmax, threshold, flags, stream);
+}
+
+vr_status vr_barcodes_dists_device(const float* lower_tri, int64_t n, int32_t dmax, float threshold, uint32_t flags,
+                                   void* stream, vr_device_result** out) {
+    return vr::run_device(out, lower_tri, false, n, 0, dmax, threshold, flags, stream);
+}
+
+void vr_device_result_free(vr_device_result* r) {
+    if (!r) return;
+    for (int p = 0; p <= VR_MAX_DIM; ++p) {
+        if (r->pairs[p]) cudaFree(r->pairs[p]);
+        if (r->critical_edges[p]) cudaFree(r->critical_edges[p]);
+    }
+    free(r);
 }
 
 void vr_result_free(vr_result* r) {

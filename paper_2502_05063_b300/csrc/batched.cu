@@ -851,10 +851,15 @@ int tuned_slots(BatchPlan& P, cudaStream_t s, int sms, int64_t bucket) {
 }  // namespace
 }  // namespace vr
 
-extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offsets, int32_t num_clouds,
-                                         int32_t ambient_dim, int32_t dmax, float threshold, uint32_t flags,
-                                         void* stream, vr_batch_result** out) {
-    using namespace vr;
+namespace vr {
+namespace {
+
+// The batched computation; with `dres` the pairs and critical edges end in
+// device memory (dev->pairs / dev->critical_edges, cudaMalloc) instead of
+// the host arrays of *out (whose pairs / critical_edges are then NULL).
+vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clouds, int32_t ambient_dim,
+                       int32_t dmax, float threshold, uint32_t flags, void* stream, vr_batch_result** out,
+                       vr_batch_device_result* dres) {
     if (!out) return VR_ERR_INVALID_ARG;
     *out = nullptr;
     if (num_clouds < 0 || !offsets || (num_clouds > 0 && !pts) || ambient_dim < 1 || ambient_dim > BMAXDIM ||
@@ -880,7 +885,14 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
         for (int p = 0; p < 2; ++p) res->pair_offsets[p] = (int64_t*)calloc(num_clouds + 1, sizeof(int64_t));
         if (!res->thresholds || !res->pair_offsets[0] || !res->pair_offsets[1]) throw Error{VR_ERR_OOM};
         if (num_clouds == 0 || threshold < 0) {
-            for (int p = 0; p <= dmax; ++p) res->pairs[p] = (vr_pair*)malloc(sizeof(vr_pair));
+            for (int p = 0; p <= dmax; ++p) {
+                if (dres) {
+                    VR_CUDA(cudaMalloc(&dres->pairs[p], sizeof(vr_pair)));
+                    if (flags & VR_CRITICAL_EDGES) VR_CUDA(cudaMalloc(&dres->critical_edges[p], 4 * sizeof(int32_t)));
+                } else {
+                    res->pairs[p] = (vr_pair*)malloc(sizeof(vr_pair));
+                }
+            }
             for (int i = 0; i < num_clouds; ++i) res->thresholds[i] = threshold;
             *out = res;
             return VR_OK;
@@ -1008,6 +1020,21 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
             for (size_t b = 0; b < bad.size(); ++b) cnt[bad[b]] = redo[b]->count[p];
             std::vector<int64_t> off(num_clouds + 1, 0);
             for (int i = 0; i < num_clouds; ++i) off[i + 1] = off[i] + cnt[i];
+            if (dres) {
+                const int64_t tot = std::max<int64_t>(off[num_clouds], 1);
+                VR_CUDA(cudaMalloc(&dres->pairs[p], tot * sizeof(vr_pair)));
+                if (want_edges) VR_CUDA(cudaMalloc(&dres->critical_edges[p], tot * 4 * sizeof(int32_t)));
+                if (bad.empty()) {  // already in cloud order on the device
+                    VR_CUDA(cudaMemcpyAsync(dres->pairs[p], P->pairs[p], off[num_clouds] * sizeof(vr_pair),
+                                            cudaMemcpyDeviceToDevice, s));
+                    if (want_edges)
+                        VR_CUDA(cudaMemcpyAsync(dres->critical_edges[p], P->edges[p],
+                                                off[num_clouds] * 4 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+                    VR_CUDA(cudaStreamSynchronize(s));
+                    memcpy(res->pair_offsets[p], off.data(), (num_clouds + 1) * sizeof(int64_t));
+                    continue;
+                }
+            }
             res->pairs[p] = (vr_pair*)malloc(std::max<int64_t>(off[num_clouds], 1) * sizeof(vr_pair));
             if (want_edges)
                 res->critical_edges[p] = (int32_t*)malloc(std::max<int64_t>(off[num_clouds], 1) * 4 * sizeof(int32_t));
@@ -1048,10 +1075,22 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
                 }
             }
             memcpy(res->pair_offsets[p], off.data(), (num_clouds + 1) * sizeof(int64_t));
+            if (dres) {  // clouds recomputed on the host path: upload the assembled arrays
+                VR_CUDA(cudaMemcpyAsync(dres->pairs[p], res->pairs[p], off[num_clouds] * sizeof(vr_pair),
+                                        cudaMemcpyHostToDevice, s));
+                if (want_edges)
+                    VR_CUDA(cudaMemcpyAsync(dres->critical_edges[p], res->critical_edges[p],
+                                            off[num_clouds] * 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+                VR_CUDA(cudaStreamSynchronize(s));
+                free(res->pairs[p]);
+                free(res->critical_edges[p]);
+                res->pairs[p] = nullptr;
+                res->critical_edges[p] = nullptr;
+            }
         }
         for (auto r : redo) vr_result_free(r);
         (void)sumsq;
-        if (flags & VR_DEBUG_CHECKS) {
+        if ((flags & VR_DEBUG_CHECKS) && !dres) {
             // per cloud: n_i - 1 finite H0 pairs at most, one essential H0 class at least,
             // birth <= death, and the documented order within the cloud
             for (int p = 0; p <= dmax; ++p)
@@ -1080,6 +1119,53 @@ extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offset
         vr_batch_result_free(res);
         return VR_ERR_OOM;
     }
+}
+
+}  // namespace
+}  // namespace vr
+
+extern "C" vr_status vr_barcodes_batched(const float* pts, const int64_t* offsets, int32_t num_clouds,
+                                         int32_t ambient_dim, int32_t dmax, float threshold, uint32_t flags,
+                                         void* stream, vr_batch_result** out) {
+    return vr::batched_impl(pts, offsets, num_clouds, ambient_dim, dmax, threshold, flags, stream, out, nullptr);
+}
+
+extern "C" vr_status vr_barcodes_batched_device(const float* pts, const int64_t* offsets, int32_t num_clouds,
+                                                int32_t ambient_dim, int32_t dmax, float threshold, uint32_t flags,
+                                                void* stream, vr_batch_device_result** out) {
+    if (!out) return VR_ERR_INVALID_ARG;
+    *out = nullptr;
+    vr_batch_device_result* d = (vr_batch_device_result*)calloc(1, sizeof(vr_batch_device_result));
+    if (!d) return VR_ERR_OOM;
+    vr_batch_result* r = nullptr;
+    const vr_status st =
+        vr::batched_impl(pts, offsets, num_clouds, ambient_dim, dmax, threshold, flags, stream, &r, d);
+    if (st != VR_OK) {
+        vr_batch_device_result_free(d);
+        return st;
+    }
+    d->num_clouds = r->num_clouds;
+    d->dmax = r->dmax;
+    for (int p = 0; p < 2; ++p) {  // the host offsets and thresholds move over
+        d->pair_offsets[p] = r->pair_offsets[p];
+        r->pair_offsets[p] = nullptr;
+    }
+    d->thresholds = r->thresholds;
+    r->thresholds = nullptr;
+    vr_batch_result_free(r);
+    *out = d;
+    return VR_OK;
+}
+
+extern "C" void vr_batch_device_result_free(vr_batch_device_result* r) {
+    if (!r) return;
+    for (int p = 0; p < 2; ++p) {
+        free(r->pair_offsets[p]);
+        if (r->pairs[p]) cudaFree(r->pairs[p]);
+        if (r->critical_edges[p]) cudaFree(r->critical_edges[p]);
+    }
+    free(r->thresholds);
+    free(r);
 }
 
 extern "C" void vr_batch_result_free(vr_batch_result* r) {

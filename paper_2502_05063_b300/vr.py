@@ -71,6 +71,22 @@ class BatchResult(ctypes.Structure):
                 ("thresholds", ctypes.POINTER(ctypes.c_float))]
 
 
+class DeviceResult(ctypes.Structure):
+    _fields_ = [("dmax", ctypes.c_int32), ("n", ctypes.c_int64), ("threshold", ctypes.c_float),
+                ("count", ctypes.c_int64 * (VR_MAX_DIM + 1)),
+                ("pairs", ctypes.c_void_p * (VR_MAX_DIM + 1)),
+                ("critical_edges", ctypes.c_void_p * (VR_MAX_DIM + 1)),
+                ("stats", Stats * (VR_MAX_DIM + 1))]
+
+
+class BatchDeviceResult(ctypes.Structure):
+    _fields_ = [("num_clouds", ctypes.c_int32), ("dmax", ctypes.c_int32),
+                ("pair_offsets", ctypes.POINTER(ctypes.c_int64) * 2),
+                ("pairs", ctypes.c_void_p * 2),
+                ("critical_edges", ctypes.c_void_p * 2),
+                ("thresholds", ctypes.POINTER(ctypes.c_float))]
+
+
 PAIR_DTYPE = np.dtype([("birth", "<f4"), ("death", "<f4"), ("birth_simplex", "<u8"), ("death_simplex", "<i8")])
 assert PAIR_DTYPE.itemsize == ctypes.sizeof(Pair)
 
@@ -87,6 +103,15 @@ lib.vr_sort_u64.argtypes = [_vp, _vp, _i64, _i32, _vp]
 lib.vr_sort_u64_noalloc.argtypes = [_vp, _vp, _i64, _i32, _vp]
 VR_SORT_NOALLOC_MAX_KEYS = 1 << 18
 lib.vr_backward.argtypes = [_vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _vp]
+lib.vr_barcodes_points_device.argtypes = [_vp, _i64, _i32, _i32, _f32, _u32, _vp,
+                                          ctypes.POINTER(ctypes.POINTER(DeviceResult))]
+lib.vr_barcodes_dists_device.argtypes = [_vp, _i64, _i32, _f32, _u32, _vp, ctypes.POINTER(ctypes.POINTER(DeviceResult))]
+lib.vr_device_result_free.argtypes = [ctypes.POINTER(DeviceResult)]
+lib.vr_device_result_free.restype = None
+lib.vr_barcodes_batched_device.argtypes = [_vp, _vp, _i32, _i32, _i32, _f32, _u32, _vp,
+                                           ctypes.POINTER(ctypes.POINTER(BatchDeviceResult))]
+lib.vr_batch_device_result_free.argtypes = [ctypes.POINTER(BatchDeviceResult)]
+lib.vr_batch_device_result_free.restype = None
 lib.vr_probe_read_gbs.argtypes = [_i64, _i32, _vp, ctypes.POINTER(ctypes.c_double)]
 if hasattr(lib, "vr_barcodes_batched"):
     lib.vr_barcodes_batched.argtypes = [_vp, _vp, _i32, _i32, _i32, _f32, _u32, _vp,
@@ -257,3 +282,99 @@ def probe_read_gbs(nbytes: int, iters: int, stream=None) -> float:
     _check(lib.vr_probe_read_gbs(int(nbytes), int(iters), _stream_ptr(stream), ctypes.byref(out)),
            "vr_probe_read_gbs")
     return out.value
+
+
+class _DevArray:
+    """__cuda_array_interface__ view of library-owned device memory (borrowed)."""
+
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _own(ptr, count, per, torch_dtype, cols):
+    """A torch CUDA tensor (count, cols) copied from `count` records of `per`
+    bytes at a library device pointer (a device-to-device copy)."""
+    import torch
+    if count == 0 or not ptr:
+        return torch.zeros((0, cols), dtype=torch_dtype, device="cuda")
+    raw = torch.as_tensor(_DevArray(ptr, count * per), device="cuda")
+    return raw.view(torch_dtype).view(count, -1)[:, :cols].clone()
+
+
+class DeviceBarcodes:
+    """Pairs of one cloud kept on the GPU (vr_barcodes_*_device).
+
+    values[p]   torch float32 (k_p, 2) CUDA tensor of (birth, death), sorted as in Barcodes
+    simplices[p] torch int64 (k_p, 2) CUDA tensor of (birth simplex, death simplex)
+    edges[p]    torch int32 (k_p, 4) CUDA tensor of critical edges, or None
+    stats[p], threshold, counts as in Barcodes.
+    """
+
+    def __init__(self, res: DeviceResult):
+        import torch
+        self.dmax, self.n, self.threshold = res.dmax, res.n, res.threshold
+        self.values, self.simplices, self.edges, self.stats, self.counts = [], [], [], [], []
+        for p in range(res.dmax + 1):
+            k = int(res.count[p])
+            self.counts.append(k)
+            self.values.append(_own(res.pairs[p], k, PAIR_DTYPE.itemsize, torch.float32, 2))
+            sim = _own(res.pairs[p], k, PAIR_DTYPE.itemsize, torch.int64, 3)
+            self.simplices.append(sim[:, 1:3].contiguous() if k else torch.zeros((0, 2), dtype=torch.int64,
+                                                                                  device="cuda"))
+            self.edges.append(_own(res.critical_edges[p], k, 16, torch.int32, 4) if res.critical_edges[p] else None)
+            self.stats.append({f: getattr(res.stats[p], f) for f in STAT_FIELDS + TIME_FIELDS})
+
+
+def barcodes_device(points=None, dists=None, n=None, dmax=1, threshold=np.inf, flags=0, stream=None):
+    """Like barcodes(), with the pairs left on the GPU (DeviceBarcodes)."""
+    out = ctypes.POINTER(DeviceResult)()
+    if points is not None:
+        ptr, keep = _ptr_of(points)
+        code = lib.vr_barcodes_points_device(ptr, int(points.shape[0]), int(points.shape[1]), int(dmax),
+                                             float(threshold), int(flags), _stream_ptr(stream), ctypes.byref(out))
+    else:
+        ptr, keep = _ptr_of(dists)
+        if n is None:
+            m = int(dists.shape[0])
+            n = int(round((1 + (1 + 8 * m) ** 0.5) / 2))
+        code = lib.vr_barcodes_dists_device(ptr, int(n), int(dmax), float(threshold), int(flags),
+                                            _stream_ptr(stream), ctypes.byref(out))
+    _check(code, "vr_barcodes_device")
+    try:
+        return DeviceBarcodes(out.contents)
+    finally:
+        lib.vr_device_result_free(out)
+
+
+class DeviceBatchBarcodes:
+    """Pairs of many clouds on the GPU: values[p] (K_p, 2) float32 and edges[p]
+    (K_p, 4) int32 (rows of the packed point array) CUDA tensors, offsets[p]
+    host int64 (num+1,), thresholds host float32."""
+
+    def __init__(self, res: BatchDeviceResult):
+        import torch
+        nc = res.num_clouds
+        self.num_clouds, self.dmax = nc, res.dmax
+        self.thresholds = np.ctypeslib.as_array(res.thresholds, shape=(max(nc, 1),))[:nc].copy()
+        self.values, self.edges, self.offsets = [], [], []
+        for p in range(res.dmax + 1):
+            off = np.ctypeslib.as_array(res.pair_offsets[p], shape=(nc + 1,)).copy()
+            k = int(off[-1])
+            self.offsets.append(off)
+            self.values.append(_own(res.pairs[p], k, PAIR_DTYPE.itemsize, torch.float32, 2))
+            self.edges.append(_own(res.critical_edges[p], k, 16, torch.int32, 4) if res.critical_edges[p] else None)
+
+
+def barcodes_batched_device(points, offsets, dmax=1, threshold=np.inf, flags=0, stream=None):
+    """Like barcodes_batched(), with the pairs left on the GPU (DeviceBatchBarcodes)."""
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    ptr, keep = _ptr_of(points)
+    out = ctypes.POINTER(BatchDeviceResult)()
+    code = lib.vr_barcodes_batched_device(ptr, offs.ctypes.data, len(offs) - 1, int(points.shape[1]), int(dmax),
+                                          float(threshold), int(flags), _stream_ptr(stream), ctypes.byref(out))
+    _check(code, "vr_barcodes_batched_device")
+    try:
+        return DeviceBatchBarcodes(out.contents)
+    finally:
+        lib.vr_batch_device_result_free(out)
