@@ -247,6 +247,52 @@ def other_workload_rates(stream, reps=5):
     return out
 
 
+def reduction_ablation(stream, reps=3):
+    """Sec. 5.2.9 ablation: the reduction of the non-apparent columns with reduced
+    columns kept explicitly (default), with only their generators kept
+    (reduction-matrix technique, VR_REDUCE_V) and with nothing kept (oblivious,
+    VR_REDUCE_OBLIVIOUS).  Per mode and dimension: column additions and the
+    reduction's stage time (median of `reps` calls after one warm-up); the
+    pairs are the same in every mode (tested)."""
+    import numpy as np
+    import torch
+    from paper_2502_05063_b300 import synth, vr
+    modes = {"explicit_default": 0, "v_matrix": vr.VR_REDUCE_V, "oblivious": vr.VR_REDUCE_OBLIVIOUS}
+    cases = {"torus500": (torch.from_numpy(synth.WORKLOADS["torus500"]["make"]()).cuda(), None, 2, np.inf)}
+    for n in (100, 200):
+        D = synth.random_permutation_dists(n)
+        cases["randperm%d" % n] = (None, torch.from_numpy(D).cuda(), 1, float(D.max()))
+    out = {}
+    for cname, (pts, dists, dmax, thr) in cases.items():
+        res = {}
+        for mname, fl in modes.items():
+            def call():
+                if pts is not None:
+                    return vr.barcodes(points=pts, dmax=dmax, threshold=thr, flags=fl, stream=stream)
+                return vr.barcodes(dists=dists, n=int(round((1 + (1 + 8 * dists.shape[0]) ** 0.5) / 2)), dmax=dmax,
+                                   threshold=thr, flags=fl, stream=stream)
+            try:
+                call()
+                runs = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = call()
+                    e1.record(stream)
+                    e1.synchronize()
+                    runs.append((e0.elapsed_time(e1), r))
+                runs.sort(key=lambda t: t[0])
+                ms, r = runs[len(runs) // 2]
+                res[mname] = {"call_ms": ms, "dims": {"dim%d" % p: {"additions": r.stats[p]["additions"],
+                                                                    "reduced_columns": r.stats[p]["reduced"],
+                                                                    "ms_reduce": r.stats[p]["ms_reduce"]}
+                                                      for p in range(1, dmax + 1)}}
+            except Exception as e:  # noqa: BLE001  (a mode that runs out of memory is a result)
+                res[mname] = {"error": str(e)}
+        out[cname] = res
+    return out
+
+
 RANDPERM_NS = (50, 100, 200, 400, 1000, 2000, 4000, 9000)
 
 
@@ -550,6 +596,7 @@ def run_ours(args):
         line["batched"] = batched_metrics(stream)
         line["other_workloads"] = other_workload_rates(stream)
         line["randperm"] = randperm_curve(stream)
+        line["reduction_ablation"] = reduction_ablation(stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_single()
         if not args.no_batched:

@@ -73,6 +73,19 @@ typedef enum {
                                     stats[dmax].pairs counts the apparent pairs, and no pairs
                                     of dimension dmax are returned (count[dmax] = 0).
                                     Dimensions below dmax are computed in full.              */
+/* Reduction of the non-apparent columns (Sec. 5.2.9; at most one of the two;
+ * the pairs are the same in every mode, only work and memory differ):
+ *  default              a column finished with additions keeps its reduced
+ *                       column R_j: as its generators (column j of V) when it
+ *                       finished in the warp engine, explicitly (sorted front
+ *                       and unsorted back) when it finished in the block engine;
+ *  VR_REDUCE_V          every such column keeps only V_j, its generators, and a
+ *                       later column that adds R_j regenerates sum of D_g
+ *                       (the reduction-matrix technique);
+ *  VR_REDUCE_OBLIVIOUS  nothing is kept: a pivot owned by column o adds D_o
+ *                       (Algorithm 12 as printed, Lemma 5.2.10).               */
+#define VR_REDUCE_V         0x10u
+#define VR_REDUCE_OBLIVIOUS 0x20u
 
 /* One persistence pair of dimension p.  birth = diam(birth simplex),
  * death = diam(death simplex) or +INFINITY for an essential class. */
@@ -144,8 +157,11 @@ void vr_result_free(vr_result* r);
 /* Device-resident variants (for callers that keep the pairs on the GPU, such
  * as the torch autograd path): the same computation and the same pairs, in
  * the same order, but pairs[p] and critical_edges[p] are DEVICE pointers on
- * the call's device, allocated by the library (cudaMalloc) and released by
- * vr_device_result_free; counts, stats and the threshold are on the host.
+ * the call's device, allocated by the library in stream order on `stream`
+ * (cudaMallocAsync) and released by vr_device_result_free in that stream's
+ * order (cudaFreeAsync; the stream must still exist then, and work queued on
+ * it before the free may still read the arrays); counts, stats and the
+ * threshold are on the host.  The arrays are complete when the call returns.
  * The pairs are ordered and filtered on the device; nothing but counts goes
  * to the host.  Arguments and errors as vr_barcodes_points / _dists. */
 typedef struct {
@@ -156,6 +172,7 @@ typedef struct {
     vr_pair* pairs[VR_MAX_DIM + 1];            /* device, count[p] entries (at least one allocated) */
     int32_t* critical_edges[VR_MAX_DIM + 1];   /* device, 4 per pair, if VR_CRITICAL_EDGES; else NULL */
     vr_stats stats[VR_MAX_DIM + 1];
+    void* stream;                              /* the call's stream (used by the free) */
 } vr_device_result;
 
 vr_status vr_barcodes_points_device(const float* pts, int64_t n, int32_t ambient_dim, int32_t dmax,
@@ -188,9 +205,9 @@ vr_status vr_barcodes_batched(const float* pts, const int64_t* offsets, int32_t 
 void vr_batch_result_free(vr_batch_result* r);
 
 /* Device-resident variant of vr_barcodes_batched: the same pairs in the same
- * order; pairs[p] and critical_edges[p] are device pointers (cudaMalloc by
- * the library), pair_offsets and thresholds host arrays, all released by
- * vr_batch_device_result_free. */
+ * order; pairs[p] and critical_edges[p] are device pointers (allocated and,
+ * by vr_batch_device_result_free, released in the order of `stream`, as for
+ * vr_device_result), pair_offsets and thresholds host arrays. */
 typedef struct {
     int32_t num_clouds;
     int32_t dmax;
@@ -198,6 +215,7 @@ typedef struct {
     vr_pair* pairs[2];                  /* device                                          */
     int32_t* critical_edges[2];         /* device, 4 per pair if VR_CRITICAL_EDGES, else NULL */
     float* thresholds;                  /* host, float[num_clouds]                          */
+    void* stream;                       /* the call's stream (used by the free)             */
 } vr_batch_device_result;
 
 vr_status vr_barcodes_batched_device(const float* pts, const int64_t* offsets, int32_t num_clouds,

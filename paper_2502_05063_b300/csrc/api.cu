@@ -235,7 +235,8 @@ __global__ void k_emit_gather(const PairRec* __restrict__ recs, int64_t cnt, con
 
 // Pairs of dimension p as the host path would return them (zero-length ones
 // dropped unless keep_zero; sorted by (birth, death, birth simplex)), in
-// device memory that outlives the call (cudaMalloc; vr_device_result_free).
+// device memory that outlives the call (stream-ordered allocation on the
+// call's stream, released by vr_device_result_free on that stream).
 static int64_t device_emit(Workspace& ws, HostScratch& hs, const PairRec* recs, int64_t num, int p,
                            const RankMatrix& R, const Binom& B, const float* values, bool keep_zero,
                            bool want_edges, vr_pair** out, int32_t** edges) {
@@ -255,8 +256,9 @@ static int64_t device_emit(Workspace& ws, HostScratch& hs, const PairRec* recs, 
         VR_CUDA(cudaMemcpyAsync(&hs.p[40], kept, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         VR_CUDA(cudaStreamSynchronize(s));
         cnt = hs.p[40];
-        VR_CUDA(cudaMalloc(out, (size_t)std::max<int64_t>(cnt, 1) * sizeof(vr_pair)));
-        if (want_edges) VR_CUDA(cudaMalloc(edges, (size_t)std::max<int64_t>(cnt, 1) * 4 * sizeof(int32_t)));
+        VR_CUDA(cudaMallocAsync((void**)out, (size_t)std::max<int64_t>(cnt, 1) * sizeof(vr_pair), s));
+        if (want_edges)
+            VR_CUDA(cudaMallocAsync((void**)edges, (size_t)std::max<int64_t>(cnt, 1) * 4 * sizeof(int32_t), s));
         if (cnt > 0) {
             PairRec* sorted = ws.alloc_n<PairRec>(cnt);
             k_emit_gather<<<blocks, 256, 0, s>>>(recs, cnt, idx, values, sorted, *out);
@@ -267,8 +269,8 @@ static int64_t device_emit(Workspace& ws, HostScratch& hs, const PairRec* recs, 
             }
         }
     } else {
-        VR_CUDA(cudaMalloc(out, sizeof(vr_pair)));
-        if (want_edges) VR_CUDA(cudaMalloc(edges, 4 * sizeof(int32_t)));
+        VR_CUDA(cudaMallocAsync((void**)out, sizeof(vr_pair), s));
+        if (want_edges) VR_CUDA(cudaMallocAsync((void**)edges, 4 * sizeof(int32_t), s));
     }
     return cnt;
 }
@@ -581,6 +583,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         in.rank_bits = rank_bits;
         in.cols = keys;
         in.num_cols = nna;
+        in.mode = (flags & VR_REDUCE_V) ? 1 : (flags & VR_REDUCE_OBLIVIOUS) ? 2 : 0;
         ReduceOut out;
         out.pairs = pr;
         out.num_pairs = rc;
@@ -641,8 +644,10 @@ static vr_status run_guarded(vr_result** out, const float* data, bool is_points,
     if (!data && n > 1) return VR_ERR_INVALID_ARG;
     if (n < 1 || n > (1 << 16) || dmax < 0 || dmax > VR_MAX_DIM || std::isnan(threshold)) return VR_ERR_INVALID_ARG;
     if (is_points && (amb < 1 || amb > 1024)) return VR_ERR_INVALID_ARG;
-    if (flags & ~(uint32_t)(VR_KEEP_ZERO_LENGTH | VR_CRITICAL_EDGES | VR_DEBUG_CHECKS | VR_APPARENT_ONLY))
+    if (flags & ~(uint32_t)(VR_KEEP_ZERO_LENGTH | VR_CRITICAL_EDGES | VR_DEBUG_CHECKS | VR_APPARENT_ONLY |
+                            VR_REDUCE_V | VR_REDUCE_OBLIVIOUS))
         return VR_ERR_INVALID_ARG;
+    if ((flags & VR_REDUCE_V) && (flags & VR_REDUCE_OBLIVIOUS)) return VR_ERR_INVALID_ARG;
     // simplex indices of dimension dmax+1 must fit 63 bits (checked before any device work)
     if (binom_host(n, dmax + 2) >= (1ull << 63)) return VR_ERR_INDEX_OVERFLOW;
     try {
@@ -680,10 +685,10 @@ static vr_status run_guarded(vr_result** out, const float* data, bool is_points,
     }
 }
 
-static void free_devout(DevOut& dv) {
+static void free_devout(DevOut& dv, cudaStream_t s) {
     for (int p = 0; p <= VR_MAX_DIM; ++p) {
-        if (dv.pairs[p]) cudaFree(dv.pairs[p]);
-        if (dv.edges[p]) cudaFree(dv.edges[p]);
+        if (dv.pairs[p]) cudaFreeAsync(dv.pairs[p], s);
+        if (dv.edges[p]) cudaFreeAsync(dv.edges[p], s);
         dv.pairs[p] = nullptr;
         dv.edges[p] = nullptr;
     }
@@ -697,13 +702,14 @@ static vr_status run_device(vr_device_result** out, const float* data, bool is_p
     memset(&dv, 0, sizeof dv);
     vr_result* r = nullptr;
     vr_status st = run_guarded(&r, data, is_points, n, amb, dmax, threshold, flags, stream, &dv);
+    cudaStream_t s = (cudaStream_t)stream;
     if (st != VR_OK) {
-        free_devout(dv);
+        free_devout(dv, s);
         return st;
     }
     vr_device_result* d = (vr_device_result*)calloc(1, sizeof(vr_device_result));
     if (!d) {
-        free_devout(dv);
+        free_devout(dv, s);
         vr_result_free(r);
         return VR_ERR_OOM;
     }
@@ -714,15 +720,17 @@ static vr_status run_device(vr_device_result** out, const float* data, bool is_p
     memcpy(d->stats, r->stats, sizeof d->stats);
     vr_result_free(r);
     const bool want_edges = flags & VR_CRITICAL_EDGES;
+    d->stream = stream;
     for (int p = 0; p <= dmax; ++p) {
-        if (!dv.pairs[p] && cudaMalloc(&dv.pairs[p], sizeof(vr_pair)) != cudaSuccess) st = VR_ERR_OOM;
-        if (want_edges && !dv.edges[p] && cudaMalloc(&dv.edges[p], 4 * sizeof(int32_t)) != cudaSuccess)
+        if (!dv.pairs[p] && cudaMallocAsync((void**)&dv.pairs[p], sizeof(vr_pair), s) != cudaSuccess) st = VR_ERR_OOM;
+        if (want_edges && !dv.edges[p] && cudaMallocAsync((void**)&dv.edges[p], 4 * sizeof(int32_t), s) != cudaSuccess)
             st = VR_ERR_OOM;
         d->pairs[p] = dv.pairs[p];
         d->critical_edges[p] = want_edges ? dv.edges[p] : nullptr;
     }
+    if (st == VR_OK && cudaStreamSynchronize(s) != cudaSuccess) st = VR_ERR_CUDA;
     if (st != VR_OK) {
-        free_devout(dv);
+        free_devout(dv, s);
         free(d);
         return st;
     }
@@ -760,8 +768,8 @@ vr_status vr_barcodes_dists_device(const float* lower_tri, int64_t n, int32_t dm
 void vr_device_result_free(vr_device_result* r) {
     if (!r) return;
     for (int p = 0; p <= VR_MAX_DIM; ++p) {
-        if (r->pairs[p]) cudaFree(r->pairs[p]);
-        if (r->critical_edges[p]) cudaFree(r->critical_edges[p]);
+        if (r->pairs[p]) cudaFreeAsync(r->pairs[p], (cudaStream_t)r->stream);
+        if (r->critical_edges[p]) cudaFreeAsync(r->critical_edges[p], (cudaStream_t)r->stream);
     }
     free(r);
 }

@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
         c.pool = A.pool + slot * POOLCAP;
         c.pool_used = A.pool_used + slot;
         c.pool_cap = POOLCAP;
-        c.rc_off = A.rc_off + slot * (int64_t)CCAP;
+        c.rc_ptr = A.rc_off + slot * (int64_t)CCAP;
+        c.mode = MODE_EXPLICIT;
         c.rc_len = A.rc_len + slot * (int64_t)CCAP;
         uint32_t* adds_j = A.adds + slot * (int64_t)CCAP;
         for (uint64_t i = threadIdx.x; i < hsz; i += HT) c.hkeys[i] = EMPTY;
@@ -887,8 +888,9 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
         if (num_clouds == 0 || threshold < 0) {
             for (int p = 0; p <= dmax; ++p) {
                 if (dres) {
-                    VR_CUDA(cudaMalloc(&dres->pairs[p], sizeof(vr_pair)));
-                    if (flags & VR_CRITICAL_EDGES) VR_CUDA(cudaMalloc(&dres->critical_edges[p], 4 * sizeof(int32_t)));
+                    VR_CUDA(cudaMallocAsync((void**)&dres->pairs[p], sizeof(vr_pair), s));
+                    if (flags & VR_CRITICAL_EDGES)
+                        VR_CUDA(cudaMallocAsync((void**)&dres->critical_edges[p], 4 * sizeof(int32_t), s));
                 } else {
                     res->pairs[p] = (vr_pair*)malloc(sizeof(vr_pair));
                 }
@@ -1022,8 +1024,8 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
             for (int i = 0; i < num_clouds; ++i) off[i + 1] = off[i] + cnt[i];
             if (dres) {
                 const int64_t tot = std::max<int64_t>(off[num_clouds], 1);
-                VR_CUDA(cudaMalloc(&dres->pairs[p], tot * sizeof(vr_pair)));
-                if (want_edges) VR_CUDA(cudaMalloc(&dres->critical_edges[p], tot * 4 * sizeof(int32_t)));
+                VR_CUDA(cudaMallocAsync((void**)&dres->pairs[p], tot * sizeof(vr_pair), s));
+                if (want_edges) VR_CUDA(cudaMallocAsync((void**)&dres->critical_edges[p], tot * 4 * sizeof(int32_t), s));
                 if (bad.empty()) {  // already in cloud order on the device
                     VR_CUDA(cudaMemcpyAsync(dres->pairs[p], P->pairs[p], off[num_clouds] * sizeof(vr_pair),
                                             cudaMemcpyDeviceToDevice, s));
@@ -1137,6 +1139,7 @@ extern "C" vr_status vr_barcodes_batched_device(const float* pts, const int64_t*
     *out = nullptr;
     vr_batch_device_result* d = (vr_batch_device_result*)calloc(1, sizeof(vr_batch_device_result));
     if (!d) return VR_ERR_OOM;
+    d->stream = stream;
     vr_batch_result* r = nullptr;
     const vr_status st =
         vr::batched_impl(pts, offsets, num_clouds, ambient_dim, dmax, threshold, flags, stream, &r, d);
@@ -1161,8 +1164,8 @@ extern "C" void vr_batch_device_result_free(vr_batch_device_result* r) {
     if (!r) return;
     for (int p = 0; p < 2; ++p) {
         free(r->pair_offsets[p]);
-        if (r->pairs[p]) cudaFree(r->pairs[p]);
-        if (r->critical_edges[p]) cudaFree(r->critical_edges[p]);
+        if (r->pairs[p]) cudaFreeAsync(r->pairs[p], (cudaStream_t)r->stream);
+        if (r->critical_edges[p]) cudaFreeAsync(r->critical_edges[p], (cudaStream_t)r->stream);
     }
     free(r->thresholds);
     free(r);

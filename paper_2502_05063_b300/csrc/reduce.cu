@@ -89,7 +89,8 @@ k_reduce_round(Ctx c, const uint32_t* __restrict__ U, int64_t u, int budget, uin
 __device__ void finalize_rows(const Ctx& c, const Emit& e, const uint32_t* __restrict__ U, int64_t u,
                               const uint64_t* cur_key, const uint8_t* status, const uint32_t* adds,
                               uint32_t* __restrict__ Unext, unsigned long long* __restrict__ u_next,
-                              unsigned long long* __restrict__ first_status) {
+                              unsigned long long* __restrict__ first_status, const HeavyState* hv = nullptr,
+                              const uint32_t* __restrict__ slot_of = nullptr) {
     __shared__ uint64_t wmin[32];
     __shared__ uint32_t wcnt[32];
     __shared__ uint64_t carry_min;
@@ -132,7 +133,19 @@ __device__ void finalize_rows(const Ctx& c, const Emit& e, const uint32_t* __res
         if (excl < pm) pm = excl;
         const bool fin = valid && st == ST_COMPLETE && (key == EMPTY || key < pm);
         if (k == 0 && st == ST_OVERFLOW) *first_status = ST_OVERFLOW;  // sticky until the host clears it
-        if (fin) finish_column(c, e, j, key, __ldcg(adds + j));
+        if (fin) {
+            const uint32_t a = __ldcg(adds + j);
+            if (hv && c.mode == MODE_V) {  // the column's generators become its stored form
+                const uint32_t sl = slot_of[j];
+                if (sl != 0xFFFFFFFFu && a > 0) {
+                    c.rc_ptr[j] = (uint64_t)hv->V[sl];
+                    c.rc_len[j] = (uint32_t)__ldcg(hv->vlen + sl);
+                } else if (sl != 0xFFFFFFFFu) {
+                    c.rc_len[j] = 0;  // D_j itself
+                }
+            }
+            finish_column(c, e, j, key, a);
+        }
         const bool keep = valid && !fin;
         const uint32_t kb = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) wcnt[wid] = __popc(kb);
@@ -182,14 +195,19 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
     __syncthreads();
     uint32_t adds;
     bool ok = true;
+    const bool vmode = c.mode == MODE_V;
+    uint64_t* V = vmode ? hs.V[slot] : nullptr;
+    const int64_t vcap = vmode ? hs.vcap[slot] : 0;
     if (!hs.init[slot]) {
-        if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.holes = 0; S.Ks = EMPTY; S.cur = 0; }
+        if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.holes = 0; S.Ks = EMPTY; S.cur = 0; S.vlen = 0; }
         __syncthreads();
         adds = 0;
         ok = heavy_add_coboundary<P>(c, S, B, bcap, s);
+        if (ok && vmode) ok = heavy_v_append1(S, V, vcap, self_key);
     } else {
         if (threadIdx.x == 0) {
             S.fsize = hs.fsize[slot]; S.bsize = hs.bsize[slot]; S.holes = hs.holes[slot]; S.Ks = hs.Ks[slot]; S.cur = 0;
+            S.vlen = vmode ? hs.vlen[slot] : 0;
         }
         adds = hs.adds[slot];
         __syncthreads();
@@ -225,24 +243,33 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
         if (kind == 1) {
             const int64_t opos = S.opos;
             const uint32_t os = slot_of[opos];
-            if (os != 0xFFFFFFFFu && hs.init[os] && hs.adds[os] > 0) {
+            if (c.mode == MODE_EXPLICIT && os != 0xFFFFFFFFu && hs.init[os] && hs.adds[os] > 0) {
                 // owner finished by this engine: add its reduced form, front then back
                 ok = heavy_add_multiset(S, B, bcap, hs.F + (int64_t)os * FC, hs.fsize[os]) &&
                      heavy_add_multiset(S, B, bcap, hs.B[os], hs.bsize[os]);
-            } else if (c.rc_len[opos]) {
+            } else if (c.mode != MODE_OBLIVIOUS && c.rc_len[opos]) {
+                // R_o from its generators (column o of V)
                 ok = heavy_add_stored<P>(c, S, B, bcap, opos);
+                if (ok && vmode)
+                    ok = heavy_v_append(S, V, vcap, reinterpret_cast<const uint64_t*>(c.rc_ptr[opos]),
+                                        c.rc_len[opos]);
             } else {
+                // D_o: the owner needed no addition, or (oblivious) nothing of R_o is kept
                 Simplex<P> o;
                 load_col<P>(c, c.cols[opos], o);
                 ok = heavy_add_coboundary<P>(c, S, B, bcap, o);
+                if (ok && vmode) ok = heavy_v_append1(S, V, vcap, c.cols[opos]);
             }
         } else {
+            // the probe's candidate s' is overwritten when the merge probes the next pivot
+            const uint64_t okey = vmode ? probed_owner_key<P>(c, S) : 0;
             const int r = heavy_apparent_add<P>(c, S, B, bcap, self_key, &pre);
             if (r < 0) {  // s' is not apparent: the pivot has no owner, the column is complete
                 if (hs.prof && threadIdx.x == 0) S.tp[15] += clock64();
                 break;
             }
             ok = r > 0;
+            if (ok && vmode) ok = heavy_v_append1(S, V, vcap, okey);
         }
         ++adds;
         ++done;
@@ -280,6 +307,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
         hs.holes[slot] = S.holes;
         hs.Ks[slot] = S.Ks;
         hs.adds[slot] = adds;
+        if (vmode) hs.vlen[slot] = S.vlen;
         hs.init[slot] = ok ? 1 : 0;  // an overflowed column restarts from scratch
         cur_key[j] = key;
         status[j] = st;
@@ -309,19 +337,24 @@ k_reduce_heavy(Ctx c, Emit e, const uint32_t* __restrict__ U, const unsigned lon
     __syncthreads();
     if (!last) return;
     __threadfence();
-    finalize_rows(c, e, U, u, cur_key, status, adds_out, Unext, d_unext, first_status);
+    finalize_rows(c, e, U, u, cur_key, status, adds_out, Unext, d_unext, first_status, &hs, slot_of);
     if (threadIdx.x == 0) *done = 0;  // ready for the next round (launched after this kernel ends)
 }
 
 // Slot k for column U[k], with the k-th back buffer of `arena` (bcap rows each).
 __global__ void k_assign_slots(const uint32_t* __restrict__ U, int64_t u, uint32_t* __restrict__ slot_of,
                                uint8_t* __restrict__ init, uint64_t* arena, int64_t bcap, uint64_t** B,
-                               int64_t* __restrict__ bc) {
+                               int64_t* __restrict__ bc, uint64_t* varena, int64_t vcap, uint64_t** V,
+                               int64_t* __restrict__ vc) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x) {
         slot_of[U[k]] = (uint32_t)k;
         init[k] = 0;
         B[k] = arena + k * bcap;
         bc[k] = bcap;
+        if (varena) {
+            V[k] = varena + k * vcap;
+            vc[k] = vcap;
+        }
     }
 }
 
@@ -329,12 +362,17 @@ __global__ void k_assign_slots(const uint32_t* __restrict__ U, int64_t u, uint32
 // new arena; finished columns keep their slots, buffers and reduced forms.
 __global__ void k_regrow_slots(const uint32_t* __restrict__ U, int64_t u, const uint32_t* __restrict__ slot_of,
                                uint8_t* __restrict__ init, uint64_t* arena, int64_t bcap, uint64_t** B,
-                               int64_t* __restrict__ bc) {
+                               int64_t* __restrict__ bc, uint64_t* varena, int64_t vcap, uint64_t** V,
+                               int64_t* __restrict__ vc) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t slot = slot_of[U[k]];
         init[slot] = 0;
         B[slot] = arena + k * bcap;
         bc[slot] = bcap;
+        if (varena) {
+            V[slot] = varena + k * vcap;
+            vc[slot] = vcap;
+        }
     }
 }
 
@@ -413,10 +451,18 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         h.adds = ws.alloc_n<uint32_t>(nslot);
         h.holes = ws.alloc_n<int64_t>(nslot);
         h.prof = log_enabled() ? ws.zeros_n<unsigned long long>(8) : nullptr;
+        // V mode: each slot's generator list, from an arena of 2^26 entries (grown
+        // with the back buffers, up to 2^30 entries in all)
+        const bool vmode = c.mode == MODE_V;
+        int64_t vcap = std::max<int64_t>((int64_t)1 << 12, std::min<int64_t>((int64_t)1 << 22, ((int64_t)1 << 26) / nslot));
+        h.V = vmode ? ws.alloc_n<uint64_t*>(nslot) : nullptr;
+        h.vcap = vmode ? ws.alloc_n<int64_t>(nslot) : nullptr;
+        h.vlen = vmode ? ws.zeros_n<int64_t>(nslot) : nullptr;
         uint32_t* slot_of = ws.alloc_n<uint32_t>(m);
         VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));  // no slot: phase-1 columns
         k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(
-            U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)nslot * bcap), bcap, h.B, h.bcap);
+            U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)nslot * bcap), bcap, h.B, h.bcap,
+            vmode ? ws.alloc_n<uint64_t>((size_t)nslot * vcap) : nullptr, vcap, h.V, h.vcap);
         int budget = 64;
         // Columns are finalized between rounds only, so a round that runs as
         // long as its longest column would keep columns it unblocks idle; a
@@ -487,11 +533,16 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 const int64_t nb = std::max<int64_t>(2 * bcap, arena / u) & ~(int64_t)15;
                 if ((double)nb * (double)u > (double)((int64_t)1 << 31)) throw Error{VR_ERR_OOM};
                 bcap = nb;
+                if (vmode) {
+                    vcap = std::max<int64_t>(2 * vcap, ((int64_t)1 << 26) / u);
+                    if ((double)vcap * (double)u > (double)((int64_t)1 << 30)) throw Error{VR_ERR_OOM};
+                }
                 if (log_enabled())
                     fprintf(stderr, "[vr] dim%d regrowth: %lld unfinished columns restart with %lld rows each\n", P,
                             (long long)u, (long long)bcap);
                 k_regrow_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(
-                    U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)u * bcap), bcap, h.B, h.bcap);
+                    U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)u * bcap), bcap, h.B, h.bcap,
+                    vmode ? ws.alloc_n<uint64_t>((size_t)u * vcap) : nullptr, vcap, h.V, h.vcap);
                 VR_CUDA(cudaGetLastError());
             }
         }
@@ -547,7 +598,8 @@ void run_reduction(const ReduceIn& in, const ReduceOut& out, bool keep_zero, Wor
     c.pool_cap = in.num_cols * RGEN;  // a column stores at most RGEN generators, once
     c.pool = ws.alloc_n<uint64_t>((size_t)c.pool_cap);
     c.pool_used = ws.zeros_n<unsigned long long>(1);
-    c.rc_off = ws.alloc_n<uint64_t>((size_t)in.num_cols);
+    c.rc_ptr = ws.alloc_n<uint64_t>((size_t)in.num_cols);
+    c.mode = in.mode;
     c.rc_len = ws.zeros_n<uint32_t>((size_t)in.num_cols);
     Emit e;
     e.pairs = out.pairs;

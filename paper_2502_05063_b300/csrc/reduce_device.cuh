@@ -29,14 +29,20 @@ struct Ctx {
     uint32_t* hvals;   // column position
     uint64_t hmask;
     int* err;
-    // finished columns that needed additions keep their reduced form R_j here,
-    // so a later column adds R_j (standard reduction) instead of D_j
+    // finished columns that needed additions keep their reduced form R_j as
+    // its generators (column j of V, R_j = sum of D_g), so a later column adds
+    // R_j (standard reduction) instead of D_j
     uint64_t* pool;
     unsigned long long* pool_used;
     int64_t pool_cap;
-    uint64_t* rc_off;  // per column position
+    uint64_t* rc_ptr;  // per column position: device address of its generator list
     uint32_t* rc_len;  // 0: the column is its own coboundary D_j
+    // reduction mode (Sec. 5.2.9): 0 = phase-2 columns keep R_j explicitly
+    // (front and back), 1 = every column keeps V_j (generators) only,
+    // 2 = oblivious (Algorithm 12 as printed: nothing is kept, owners add D_o)
+    int mode;
 };
+constexpr int MODE_EXPLICIT = 0, MODE_V = 1, MODE_OBLIVIOUS = 2;
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33;
@@ -245,13 +251,14 @@ template <int P>
 __device__ void store_generators(const Ctx& c, int64_t j, const Simplex<P>* gs, int m) {
     const int lane = threadIdx.x & 31;
     unsigned long long off = 0;
+    if (c.mode == MODE_OBLIVIOUS) return;  // Algorithm 12 keeps no reduced form
     if (lane == 0) off = atomicAdd(c.pool_used, (unsigned long long)m);
     off = __shfl_sync(0xffffffffu, off, 0);
     const bool fits = (int64_t)(off + m) <= c.pool_cap;
     if (fits && lane < m) c.pool[off + lane] = col_key<P>(c, gs[lane]);
     __syncwarp();
     if (lane == 0) {
-        c.rc_off[j] = off;
+        c.rc_ptr[j] = (uint64_t)(c.pool + off);
         c.rc_len[j] = fits ? (uint32_t)m : 0u;
         // without its reduced form a later column could only add D_j, which need
         // not cancel the shared pivot: report the shortage instead
@@ -442,6 +449,12 @@ struct HeavyState {
     uint32_t* adds;
     int64_t* holes;    // per slot: holes (EMPTY rows) in B
     unsigned long long* prof;  // VR_LOG only: cycles {refill, lookup, add, resume}, counts {adds, lookups}
+    // V mode: per slot, the column's generators so far (an unsorted multiset of
+    // column keys: j itself, then every simplex whose coboundary was added;
+    // duplicates cancel when the coboundaries are generated)
+    uint64_t** V;
+    int64_t* vcap;
+    int64_t* vlen;
 };
 
 // VR_LOG instrumentation of the block engine (-DVR_HPROF builds): {refills, rows to front, rows
@@ -459,6 +472,7 @@ struct HeavySmem {
     int64_t bsize;
     int64_t holes;         // EMPTY rows in B (left by refills)
     int64_t opos;
+    int64_t vlen;          // V mode: generators recorded so far
     int fsize;
     int cur;               // which buf holds the front
     int flag;
@@ -1164,7 +1178,7 @@ __device__ bool heavy_flush_stage(HeavySmem& S, uint64_t* B, int64_t bcap, int c
 // -- one merge for several coboundaries instead of one addition each.
 template <int P>
 __device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, int64_t opos) {
-    const uint64_t* gk = c.pool + c.rc_off[opos];
+    const uint64_t* gk = reinterpret_cast<const uint64_t*>(c.rc_ptr[opos]);
     const int64_t len = c.rc_len[opos];
     int sc = 0;  // rows in the stage
     for (int64_t i = 0; i < len; ++i) {
@@ -1256,6 +1270,38 @@ __device__ bool heavy_add_multiset(HeavySmem& S, uint64_t* B, int64_t bcap, cons
     const bool ok = sc == 0 || heavy_flush_stage(S, B, bcap, sc);
     HPROF_LAP(3);
     return ok;
+}
+
+// V mode: append `len` generator keys to the column's list; false if it has
+// no room (the column then restarts with larger buffers).
+__device__ bool heavy_v_append(HeavySmem& S, uint64_t* V, int64_t vcap, const uint64_t* src, int64_t len) {
+    const int64_t at = S.vlen;
+    if (at + len > vcap) return false;
+    for (int64_t i = threadIdx.x; i < len; i += HT) V[at + i] = src[i];
+    __syncthreads();  // every thread has read S.vlen
+    if (threadIdx.x == 0) S.vlen = at + len;
+    __syncthreads();
+    return true;
+}
+__device__ bool heavy_v_append1(HeavySmem& S, uint64_t* V, int64_t vcap, uint64_t key) {
+    const int64_t at = S.vlen;
+    if (at + 1 > vcap) return false;
+    __syncthreads();  // every thread has read S.vlen
+    if (threadIdx.x == 0) {
+        V[at] = key;
+        S.vlen = at + 1;
+    }
+    __syncthreads();
+    return true;
+}
+// Column key of the candidate apparent owner s' found by the last probe
+// (S.ov[0..P], diameter rank S.orank).
+template <int P>
+__device__ uint64_t probed_owner_key(const Ctx& c, const HeavySmem& S) {
+    uint64_t cidx = 0;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) cidx += c.B(S.ov[q], q + 1);
+    return ((~(uint64_t)S.orank & c.rmask) << c.cb) | cidx;
 }
 
 // Owner probe for pivot row rk: 1 = the pivot of a finished column (in

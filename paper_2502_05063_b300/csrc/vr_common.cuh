@@ -269,6 +269,7 @@ struct ReduceIn {
     int rank_bits;
     const uint64_t* cols; // sorted column keys, num_cols
     int64_t num_cols;
+    int mode;             // 0: explicit reduced columns, 1: V (generators), 2: oblivious (Sec. 5.2.9)
 };
 struct ReduceOut {
     PairRec* pairs;               // capacity num_cols

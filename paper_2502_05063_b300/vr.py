@@ -27,6 +27,8 @@ VR_KEEP_ZERO_LENGTH = 0x1
 VR_CRITICAL_EDGES = 0x2
 VR_DEBUG_CHECKS = 0x4
 VR_APPARENT_ONLY = 0x8
+VR_REDUCE_V = 0x10
+VR_REDUCE_OBLIVIOUS = 0x20
 
 STATUS = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_OOM", 3: "VR_ERR_INDEX_OVERFLOW",
           4: "VR_ERR_CUDA", 5: "VR_ERR_TIMEOUT", 6: "VR_ERR_INTERNAL"}
@@ -76,7 +78,7 @@ class DeviceResult(ctypes.Structure):
                 ("count", ctypes.c_int64 * (VR_MAX_DIM + 1)),
                 ("pairs", ctypes.c_void_p * (VR_MAX_DIM + 1)),
                 ("critical_edges", ctypes.c_void_p * (VR_MAX_DIM + 1)),
-                ("stats", Stats * (VR_MAX_DIM + 1))]
+                ("stats", Stats * (VR_MAX_DIM + 1)), ("stream", ctypes.c_void_p)]
 
 
 class BatchDeviceResult(ctypes.Structure):
@@ -84,7 +86,7 @@ class BatchDeviceResult(ctypes.Structure):
                 ("pair_offsets", ctypes.POINTER(ctypes.c_int64) * 2),
                 ("pairs", ctypes.c_void_p * 2),
                 ("critical_edges", ctypes.c_void_p * 2),
-                ("thresholds", ctypes.POINTER(ctypes.c_float))]
+                ("thresholds", ctypes.POINTER(ctypes.c_float)), ("stream", ctypes.c_void_p)]
 
 
 PAIR_DTYPE = np.dtype([("birth", "<f4"), ("death", "<f4"), ("birth_simplex", "<u8"), ("death_simplex", "<i8")])
@@ -292,6 +294,13 @@ class _DevArray:
                                          "version": 3, "strides": None}
 
 
+def _copies_done():
+    """The copies out of a device result were queued on torch's current stream,
+    the result is freed in the order of the call's stream: let them finish."""
+    import torch
+    torch.cuda.current_stream().synchronize()
+
+
 def _own(ptr, count, per, torch_dtype, cols):
     """A torch CUDA tensor (count, cols) copied from `count` records of `per`
     bytes at a library device pointer (a device-to-device copy)."""
@@ -344,6 +353,7 @@ def barcodes_device(points=None, dists=None, n=None, dmax=1, threshold=np.inf, f
     try:
         return DeviceBarcodes(out.contents)
     finally:
+        _copies_done()
         lib.vr_device_result_free(out)
 
 
@@ -377,4 +387,5 @@ def barcodes_batched_device(points, offsets, dmax=1, threshold=np.inf, flags=0, 
     try:
         return DeviceBatchBarcodes(out.contents)
     finally:
+        _copies_done()
         lib.vr_batch_device_result_free(out)
