@@ -259,7 +259,7 @@ def reduction_ablation(stream, reps=3):
     from paper_2502_05063_b300 import synth, vr
     modes = {"explicit_default": 0, "v_matrix": vr.VR_REDUCE_V, "oblivious": vr.VR_REDUCE_OBLIVIOUS}
     cases = {"torus500": (torch.from_numpy(synth.WORKLOADS["torus500"]["make"]()).cuda(), None, 2, np.inf)}
-    for n in (100, 200):
+    for n in (100,):
         D = synth.random_permutation_dists(n)
         cases["randperm%d" % n] = (None, torch.from_numpy(D).cuda(), 1, float(D.max()))
     out = {}

@@ -90,9 +90,12 @@ __device__ void finalize_rows(const Ctx& c, const Emit& e, const uint32_t* __res
                               const uint64_t* cur_key, const uint8_t* status, const uint32_t* adds,
                               uint32_t* __restrict__ Unext, unsigned long long* __restrict__ u_next,
                               unsigned long long* __restrict__ first_status, const HeavyState* hv = nullptr,
-                              const uint32_t* __restrict__ slot_of = nullptr) {
+                              uint32_t* __restrict__ slot_of = nullptr) {
     __shared__ uint64_t wmin[32];
     __shared__ uint32_t wcnt[32];
+    __shared__ uint32_t rel_j[1024], rel_s[1024], rel_a[1024];  // windowed: slots released by this chunk
+    __shared__ uint32_t rel_n;
+    __shared__ unsigned long long rel_off;
     __shared__ uint64_t carry_min;
     __shared__ uint32_t carry_cnt;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -133,18 +136,47 @@ __device__ void finalize_rows(const Ctx& c, const Emit& e, const uint32_t* __res
         if (excl < pm) pm = excl;
         const bool fin = valid && st == ST_COMPLETE && (key == EMPTY || key < pm);
         if (k == 0 && st == ST_OVERFLOW) *first_status = ST_OVERFLOW;  // sticky until the host clears it
-        if (fin) {
-            const uint32_t a = __ldcg(adds + j);
-            if (hv && c.mode == MODE_V) {  // the column's generators become its stored form
-                const uint32_t sl = slot_of[j];
-                if (sl != 0xFFFFFFFFu && a > 0) {
-                    c.rc_ptr[j] = (uint64_t)hv->V[sl];
-                    c.rc_len[j] = (uint32_t)__ldcg(hv->vlen + sl);
-                } else if (sl != 0xFFFFFFFFu) {
-                    c.rc_len[j] = 0;  // D_j itself
-                }
+        if (fin) finish_column(c, e, j, key, __ldcg(adds + j));
+        if (hv && hv->free_slots) {
+            // windowed engine: finalized columns give their slots back; in V mode
+            // their generators first move to the pool (one column at a time, by
+            // the whole block), where later columns read them as R_j
+            if (threadIdx.x == 0) rel_n = 0;
+            __syncthreads();
+            const uint32_t sl = fin ? slot_of[j] : 0xFFFFFFFFu;
+            if (sl != 0xFFFFFFFFu) {
+                const uint32_t q = atomicAdd(&rel_n, 1u);
+                rel_j[q] = j;
+                rel_s[q] = sl;
+                rel_a[q] = __ldcg(adds + j);
             }
-            finish_column(c, e, j, key, a);
+            __syncthreads();
+            const uint32_t nrel = rel_n;
+            for (uint32_t q = 0; q < nrel; ++q) {
+                const uint32_t jj = rel_j[q], ss = rel_s[q];
+                if (c.mode == MODE_V && rel_a[q] > 0) {
+                    const int64_t len = __ldcg(hv->vlen + ss);
+                    if (threadIdx.x == 0) rel_off = atomicAdd(c.pool_used, (unsigned long long)len);
+                    __syncthreads();
+                    const unsigned long long off = rel_off;
+                    const bool fits = (int64_t)(off + len) <= c.pool_cap;
+                    const uint64_t* src = hv->V[ss];
+                    if (fits)
+                        for (int64_t i = threadIdx.x; i < len; i += blockDim.x) c.pool[off + i] = __ldcg(src + i);
+                    if (threadIdx.x == 0) {
+                        c.rc_ptr[jj] = fits ? (uint64_t)(c.pool + off) : 0;
+                        c.rc_len[jj] = fits ? (uint32_t)len : 0u;
+                        if (!fits) atomicExch(c.err, DEV_CAPACITY);
+                    }
+                } else if (threadIdx.x == 0 && c.mode == MODE_V) {
+                    c.rc_len[jj] = 0;  // no addition: the column is D_j itself
+                }
+                if (threadIdx.x == 0) {
+                    hv->free_slots[atomicAdd(hv->free_top, 1)] = (int32_t)ss;
+                    slot_of[jj] = 0xFFFFFFFFu;
+                }
+                __syncthreads();
+            }
         }
         const bool keep = valid && !fin;
         const uint32_t kb = __ballot_sync(0xffffffffu, keep);
@@ -179,13 +211,32 @@ k_finalize(Ctx c, Emit e, const uint32_t* __restrict__ U, int64_t u, const uint6
 
 template <int P>
 __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64_t k,
-                             const uint32_t* __restrict__ slot_of, const HeavyState& hs, int budget,
+                             uint32_t* __restrict__ slot_of, const HeavyState& hs, int budget,
                              uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status,
                              uint32_t* __restrict__ adds_out) {
     extern __shared__ __align__(16) unsigned char hsm[];
     HeavySmem& S = *reinterpret_cast<HeavySmem*>(hsm);
+    __shared__ int64_t slot_sh;
     const int64_t j = U[k];
-    const int64_t slot = slot_of[j];
+    if (threadIdx.x == 0) {
+        int64_t sl = slot_of[j];
+        if (sl == 0xFFFFFFFFu) {  // windowed engine: the column enters the window
+            const int t = atomicSub(hs.free_top, 1) - 1;
+            if (t >= 0) {
+                sl = hs.free_slots[t];
+                slot_of[j] = (uint32_t)sl;
+                hs.init[sl] = 0;
+            } else {  // cannot happen (as many slots as window places): leave the column as it was
+                atomicAdd(hs.free_top, 1);
+                atomicExch(c.err, DEV_INTERNAL | (5 << 8));
+                sl = -1;
+            }
+        }
+        slot_sh = sl;
+    }
+    __syncthreads();
+    const int64_t slot = slot_sh;
+    if (slot < 0) return;
     uint64_t* B = hs.B[slot];
     const int64_t bcap = hs.bcap[slot];
     const uint64_t self_key = c.cols[j];
@@ -322,7 +373,7 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
 template <int P>
 __global__ void __launch_bounds__(HT, 1)
 k_reduce_heavy(Ctx c, Emit e, const uint32_t* __restrict__ U, const unsigned long long* __restrict__ d_u,
-               const uint32_t* __restrict__ slot_of, HeavyState hs, int budget,
+               uint32_t* __restrict__ slot_of, HeavyState hs, int budget,
                uint64_t* __restrict__ cur_key, uint8_t* __restrict__ status, uint32_t* __restrict__ adds_out,
                uint32_t* __restrict__ Unext, unsigned long long* __restrict__ d_unext,
                unsigned long long* __restrict__ first_status, unsigned int* __restrict__ done) {
@@ -358,6 +409,39 @@ __global__ void k_assign_slots(const uint32_t* __restrict__ U, int64_t u, uint32
     }
 }
 
+// Windowed engine: a column outside the window does not run, so no state of
+// it may read as complete (its pivot may have gained an owner since phase 1);
+// its key stays as a lower bound on its final pivot.
+__global__ void k_mark_unsettled(const uint32_t* __restrict__ U, int64_t u, uint8_t* __restrict__ status) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x)
+        status[U[k]] = ST_BUDGET;
+}
+
+__global__ void k_release_slots(const uint32_t* __restrict__ U, int64_t u, uint32_t* __restrict__ slot_of) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < u; k += (int64_t)gridDim.x * blockDim.x)
+        slot_of[U[k]] = 0xFFFFFFFFu;
+}
+
+// Windowed engine: every slot gets its buffers (the k-th of each arena) and
+// joins the free list; a regrowth calls it again with larger buffers (every
+// held slot restarts its column from scratch).
+__global__ void k_window_slots(int64_t nslot, int32_t* __restrict__ free_slots, int32_t* __restrict__ free_top,
+                               uint8_t* __restrict__ init, uint64_t* arena, int64_t bcap, uint64_t** B,
+                               int64_t* __restrict__ bc, uint64_t* varena, int64_t vcap, uint64_t** V,
+                               int64_t* __restrict__ vc, int fresh) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nslot; k += (int64_t)gridDim.x * blockDim.x) {
+        init[k] = 0;
+        B[k] = arena + k * bcap;
+        bc[k] = bcap;
+        if (varena) {
+            V[k] = varena + k * vcap;
+            vc[k] = vcap;
+        }
+        if (fresh) free_slots[k] = (int32_t)k;
+    }
+    if (fresh && blockIdx.x == 0 && threadIdx.x == 0) *free_top = (int32_t)nslot;
+}
+
 // Regrowth: the unfinished columns U[0..u) restart in the k-th buffer of a
 // new arena; finished columns keep their slots, buffers and reduced forms.
 __global__ void k_regrow_slots(const uint32_t* __restrict__ U, int64_t u, const uint32_t* __restrict__ slot_of,
@@ -380,6 +464,8 @@ __global__ void k_iota(uint32_t* U, int64_t m) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
         U[k] = (uint32_t)k;
 }
+
+constexpr int64_t HEAVY_WINDOW = 256;  // block-engine columns in flight (V and oblivious modes)
 
 // Rows of the arena the block engine's back buffers share.
 int64_t heavy_arena_rows() {
@@ -436,7 +522,11 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
     if (u > 0) {
         const size_t smem = sizeof(HeavySmem);
         VR_CUDA(cudaFuncSetAttribute(k_reduce_heavy<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int64_t nslot = u;
+        // default mode: a slot per column (finished columns keep R_j in theirs);
+        // V and oblivious modes: a window of at most HEAVY_WINDOW columns in order
+        const bool windowed = c.mode != MODE_EXPLICIT;
+        const int64_t nslot = windowed ? std::min<int64_t>(u, HEAVY_WINDOW) : u;
+        int64_t window = nslot;  // slots in circulation (shrinks when the buffers must grow past the caps)
         HeavyState h;
         // back buffers share an arena of 2^28 rows (2 GB; VR_HEAVY_ARENA_LOG2 overrides, for tests)
         const int64_t arena = heavy_arena_rows();
@@ -458,11 +548,19 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         h.V = vmode ? ws.alloc_n<uint64_t*>(nslot) : nullptr;
         h.vcap = vmode ? ws.alloc_n<int64_t>(nslot) : nullptr;
         h.vlen = vmode ? ws.zeros_n<int64_t>(nslot) : nullptr;
+        h.free_slots = windowed ? ws.alloc_n<int32_t>(nslot) : nullptr;
+        h.free_top = windowed ? ws.zeros_n<int32_t>(1) : nullptr;
         uint32_t* slot_of = ws.alloc_n<uint32_t>(m);
         VR_CUDA(cudaMemsetAsync(slot_of, 0xFF, m * sizeof(uint32_t), s));  // no slot: phase-1 columns
-        k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(
-            U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)nslot * bcap), bcap, h.B, h.bcap,
-            vmode ? ws.alloc_n<uint64_t>((size_t)nslot * vcap) : nullptr, vcap, h.V, h.vcap);
+        if (windowed) {
+            k_window_slots<<<(unsigned)((nslot + 255) / 256), 256, 0, s>>>(
+                nslot, h.free_slots, h.free_top, h.init, ws.alloc_n<uint64_t>((size_t)nslot * bcap), bcap, h.B,
+                h.bcap, vmode ? ws.alloc_n<uint64_t>((size_t)nslot * vcap) : nullptr, vcap, h.V, h.vcap, 1);
+            k_mark_unsettled<<<(unsigned)std::min<int64_t>((u + 255) / 256, 4096), 256, 0, s>>>(U, u, status);
+        } else
+            k_assign_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(
+                U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)nslot * bcap), bcap, h.B, h.bcap,
+                vmode ? ws.alloc_n<uint64_t>((size_t)nslot * vcap) : nullptr, vcap, h.V, h.vcap);
         int budget = 64;
         // Columns are finalized between rounds only, so a round that runs as
         // long as its longest column would keep columns it unblocks idle; a
@@ -493,7 +591,7 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                     VR_CUDA(cudaMemsetAsync(h.prof + 6, 0, 2 * sizeof(unsigned long long), s));
                     VR_CUDA(cudaEventRecord(ev[0], s));
                 }
-                k_reduce_heavy<P><<<(unsigned)u0, HT, smem, s>>>(c, e, U, du + cur, slot_of, h, budget,
+                k_reduce_heavy<P><<<(unsigned)(windowed ? std::min<int64_t>(u0, window) : u0), HT, smem, s>>>(c, e, U, du + cur, slot_of, h, budget,
                                                                    cur_key, status, adds, Un, du + (cur ^ 1), du + 2,
                                                                    done);
                 VR_CUDA(cudaGetLastError());
@@ -530,19 +628,39 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
                 // back buffer in this batch: the remaining columns restart from
                 // scratch with at least twice the room (the whole arena when
                 // that is more), up to 2^31 rows in all
-                const int64_t nb = std::max<int64_t>(2 * bcap, arena / u) & ~(int64_t)15;
-                if ((double)nb * (double)u > (double)((int64_t)1 << 31)) throw Error{VR_ERR_OOM};
+                int64_t held = windowed ? window : u;  // buffers to replace
+                const int64_t nb = std::max<int64_t>(2 * bcap, arena / held) & ~(int64_t)15;
+                const int64_t nv = vmode ? std::max<int64_t>(2 * vcap, ((int64_t)1 << 26) / held) : 0;
+                // windowed: fewer columns in flight rather than failing (the first
+                // column, which every round advances, keeps its place)
+                while (windowed && held > 1 && ((double)nb * (double)held > (double)((int64_t)1 << 31) ||
+                                                (double)nv * (double)held > (double)((int64_t)1 << 30)))
+                    held /= 2;
+                if ((double)nb * (double)held > (double)((int64_t)1 << 31)) throw Error{VR_ERR_OOM};
+                if (vmode && (double)nv * (double)held > (double)((int64_t)1 << 30)) throw Error{VR_ERR_OOM};
                 bcap = nb;
-                if (vmode) {
-                    vcap = std::max<int64_t>(2 * vcap, ((int64_t)1 << 26) / u);
-                    if ((double)vcap * (double)u > (double)((int64_t)1 << 30)) throw Error{VR_ERR_OOM};
-                }
+                vcap = nv;
                 if (log_enabled())
                     fprintf(stderr, "[vr] dim%d regrowth: %lld unfinished columns restart with %lld rows each\n", P,
                             (long long)u, (long long)bcap);
-                k_regrow_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(
-                    U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)u * bcap), bcap, h.B, h.bcap,
-                    vmode ? ws.alloc_n<uint64_t>((size_t)u * vcap) : nullptr, vcap, h.V, h.vcap);
+                if (windowed) {
+                    const int fresh = held < window ? 1 : 0;
+                    if (fresh) {  // a smaller window: every column gives its slot back (all restart anyway),
+                                  // and a column left outside it must not read as complete
+                        k_release_slots<<<(unsigned)std::min<int64_t>((u + 255) / 256, 4096), 256, 0, s>>>(
+                            U, u, slot_of);
+                        k_mark_unsettled<<<(unsigned)std::min<int64_t>((u + 255) / 256, 4096), 256, 0, s>>>(
+                            U, u, status);
+                    }
+                    window = held;
+                    k_window_slots<<<(unsigned)((window + 255) / 256), 256, 0, s>>>(
+                        window, h.free_slots, h.free_top, h.init, ws.alloc_n<uint64_t>((size_t)window * bcap), bcap,
+                        h.B, h.bcap, vmode ? ws.alloc_n<uint64_t>((size_t)window * vcap) : nullptr, vcap, h.V,
+                        h.vcap, fresh);
+                } else
+                    k_regrow_slots<<<(unsigned)((u + 255) / 256), 256, 0, s>>>(
+                        U, u, slot_of, h.init, ws.alloc_n<uint64_t>((size_t)u * bcap), bcap, h.B, h.bcap,
+                        nullptr, vcap, h.V, h.vcap);
                 VR_CUDA(cudaGetLastError());
             }
         }
@@ -595,7 +713,9 @@ void run_reduction(const ReduceIn& in, const ReduceOut& out, bool keep_zero, Wor
     VR_CUDA(cudaMemsetAsync(c.hkeys, 0xFF, hcap * sizeof(uint64_t), ws.stream));
     c.hmask = hcap - 1;
     c.err = out.dev_err;
-    c.pool_cap = in.num_cols * RGEN;  // a column stores at most RGEN generators, once
+    // a warp-engine column stores at most RGEN generators, once; in V mode the
+    // block engine's columns store theirs too
+    c.pool_cap = in.num_cols * RGEN + (in.mode == 1 ? ((int64_t)1 << 26) : 0);
     c.pool = ws.alloc_n<uint64_t>((size_t)c.pool_cap);
     c.pool_used = ws.zeros_n<unsigned long long>(1);
     c.rc_ptr = ws.alloc_n<uint64_t>((size_t)in.num_cols);

@@ -455,6 +455,13 @@ struct HeavyState {
     uint64_t** V;
     int64_t* vcap;
     int64_t* vlen;
+    // windowed engine (V and oblivious modes): only the first `nslot`
+    // unfinished columns hold a slot; a finalized column returns its slot
+    // here (its reduced form is not needed: its generators, if any, move to
+    // the pool) and the next column in order takes it.  NULL: every column
+    // has a fixed slot (default mode, whose finished columns keep R_j in it).
+    int32_t* free_slots;
+    int32_t* free_top;
 };
 
 // VR_LOG instrumentation of the block engine (-DVR_HPROF builds): {refills, rows to front, rows
