@@ -86,6 +86,16 @@ typedef enum {
  *                       (Algorithm 12 as printed, Lemma 5.2.10).               */
 #define VR_REDUCE_V         0x10u
 #define VR_REDUCE_OBLIVIOUS 0x20u
+/* Sparse (low-threshold) mode (Sec. 5.3.12-5.3.13, Algorithm 15; warp-based
+ * filtering, Sec. 5.5.3; capacity-driven allocation, Sec. 5.7.2): the
+ * simplices within the threshold are listed from the neighbour lists of the
+ * threshold graph, dimension by dimension, instead of enumerating all
+ * C(n, p+1) indices, and the apparent cofacet of a simplex is searched among
+ * the neighbours of its vertex of least degree.  The same pairs as without
+ * it; memory and time follow the size of the complex.  In this mode
+ * stats[p].candidates counts the listed p-simplices (above_threshold = 0).
+ * Meant for thresholds far below the enclosing radius.                        */
+#define VR_SPARSE           0x40u
 
 /* One persistence pair of dimension p.  birth = diam(birth simplex),
  * death = diam(death simplex) or +INFINITY for an essential class. */

@@ -441,7 +441,9 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
     VR_CUDA(cudaMemcpyAsync(values.data(), ri.values, ri.num_values * sizeof(float), cudaMemcpyDeviceToHost, s));
     res->threshold = (isinf(threshold) && threshold > 0) ? 0.0f : threshold;
     const RankMatrix R{ri.rank, n, ri.ld};
-    const int rank_bits = std::max(1, bits_for((uint64_t)(ri.num_values - 1)));
+    // ranks above the threshold collapse to thr + 1, so keys need only its bits
+    if ((uint64_t)thr + 1 < (uint64_t)ri.num_values) clamp_ranks(ws, ri, n, thr);
+    const int rank_bits = std::max(1, bits_for(std::min<uint64_t>((uint64_t)ri.num_values - 1, (uint64_t)thr + 1)));
     const int K = dmax + 3;
     std::vector<uint64_t> hb = host_binomials(n, K);
     uint64_t* db = ws.alloc_n<uint64_t>(hb.size());
@@ -497,14 +499,30 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
     }
 
     // ---- dimensions 1..dmax
+    // sparse mode: the simplices of the complex are listed from neighbour lists
+    // (sparse.cu) instead of enumerating every index; clearing bits of dimension
+    // p >= 2 are then indexed by position in the list of p-simplices
+    const bool sparse = flags & VR_SPARSE;
+    Neighbours nb{};
+    SimplexList L{}, Lnext{};
+    if (sparse && dmax >= 1) {
+        nb = build_neighbours(ws, R, thr, hs);
+        L = edge_list(ws, R, nb, hs);
+    }
     for (int p = 1; p <= dmax; ++p) {
-        const uint64_t ncand = binom_host(n, p + 1);
+        const uint64_t nall = binom_host(n, p + 1);
+        const uint64_t ncand = sparse ? (uint64_t)L.len : nall;
         const uint64_t nrow = binom_host(n, p + 2);
-        const int cb = std::max(1, bits_for(ncand > 0 ? ncand - 1 : 0));
+        const int cb = std::max(1, bits_for(nall > 0 ? nall - 1 : 0));
         const int rcb = std::max(1, bits_for(nrow > 0 ? nrow - 1 : 0));
         VR_CHECK(nrow != UINT64_MAX && rank_bits + cb <= 64 && rank_bits + rcb <= 63, VR_ERR_INDEX_OVERFLOW);
         uint32_t* clear_next = nullptr;
-        if (p < dmax) clear_next = ws.zeros_n<uint32_t>((nrow + 31) / 32 + 1);
+        if (sparse && p < dmax) {
+            Lnext = next_list(ws, R, B, nb, thr, L, p, rcb, hs);
+            clear_next = ws.zeros_n<uint32_t>(((uint64_t)Lnext.len + 31) / 32 + 1);
+        } else if (p < dmax) {
+            clear_next = ws.zeros_n<uint32_t>((nrow + 31) / 32 + 1);
+        }
         VR_CUDA(cudaMemsetAsync(cnt, 0, 16 * sizeof(unsigned long long), s));
         int64_t cap = (int64_t)std::max<uint64_t>(1 << 16, ncand / 16);
         if ((uint64_t)cap > ncand) cap = (int64_t)std::max<uint64_t>(ncand, 1);
@@ -524,8 +542,15 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
             ao.counters = cnt;
             ao.capacity = cap;
             ao.dev_err = dev_err;
+            if (sparse && clear_next) {
+                ao.next_list = Lnext.cidx;
+                ao.next_len = Lnext.len;
+            }
             log.mark(stage_name("launch apparent", p));
-            launch_filtration_apparent(p, R, B, thr, clear, cb, rank_bits, ncand, ao, s);
+            if (sparse)
+                launch_sparse_filtration_apparent(p, R, B, nb, L, clear, p >= 2, cb, rank_bits, ao, s);
+            else
+                launch_filtration_apparent(p, R, B, thr, clear, cb, rank_bits, ncand, ao, s);
             log.mark(stage_name("apparent", p));
             VR_CUDA(cudaMemcpyAsync(hs.p, cnt, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             VR_CUDA(cudaStreamSynchronize(s));
@@ -588,6 +613,10 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         out.pairs = pr;
         out.num_pairs = rc;
         out.clear_next = clear_next;
+        if (sparse && clear_next) {
+            out.next_list = Lnext.cidx;
+            out.next_len = Lnext.len;
+        }
         out.counters = rc + 1;
         out.dev_err = dev_err;
         log.mark(stage_name("launch reduce", p));
@@ -622,6 +651,7 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         }
         log.mark(stage_name("emit", p));
         clear = clear_next;
+        if (sparse) L = Lnext;
     }
     VR_CUDA(cudaStreamSynchronize(s));
     res->stats[0].ms_filtration = log.between("start", "ranks");
@@ -645,7 +675,7 @@ static vr_status run_guarded(vr_result** out, const float* data, bool is_points,
     if (n < 1 || n > (1 << 16) || dmax < 0 || dmax > VR_MAX_DIM || std::isnan(threshold)) return VR_ERR_INVALID_ARG;
     if (is_points && (amb < 1 || amb > 1024)) return VR_ERR_INVALID_ARG;
     if (flags & ~(uint32_t)(VR_KEEP_ZERO_LENGTH | VR_CRITICAL_EDGES | VR_DEBUG_CHECKS | VR_APPARENT_ONLY |
-                            VR_REDUCE_V | VR_REDUCE_OBLIVIOUS))
+                            VR_REDUCE_V | VR_REDUCE_OBLIVIOUS | VR_SPARSE))
         return VR_ERR_INVALID_ARG;
     if ((flags & VR_REDUCE_V) && (flags & VR_REDUCE_OBLIVIOUS)) return VR_ERR_INVALID_ARG;
     // simplex indices of dimension dmax+1 must fit 63 bits (checked before any device work)

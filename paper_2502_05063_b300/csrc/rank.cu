@@ -87,6 +87,15 @@ __global__ void k_threshold_rank(const float* __restrict__ values, const int64_t
     *out = (uint32_t)(lo - 1);
 }
 
+// Every rank above the threshold rank becomes thr + 1: no simplex with such
+// an entry is in the filtration, and every comparison the method makes with
+// one ("<= threshold", "<= diam(s)" for a simplex s of the filtration) has
+// the same outcome, so packed keys need only bits for thr + 1.
+__global__ void k_clamp_ranks(uint32_t* __restrict__ R, int64_t total, uint32_t cap) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x)
+        if (R[k] > cap) R[k] = cap;
+}
+
 static unsigned grid_for(int64_t m, int threads) {
     int64_t b = (m + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -127,6 +136,12 @@ RankInfo build_ranks(Workspace& ws, const float* lower_tri, int64_t n, HostScrat
     ri.enclosing_rank = (uint32_t)(hs.p[1] & 0xFFFFFFFFu);
     ri.num_values_dev = nv;
     return ri;
+}
+
+void clamp_ranks(Workspace& ws, const RankInfo& ri, int64_t n, uint32_t thr_rank) {
+    const int64_t total = n * ri.ld;
+    k_clamp_ranks<<<grid_for(total, 256), 256, 0, ws.stream>>>(ri.rank, total, thr_rank + 1);
+    VR_CUDA(cudaGetLastError());
 }
 
 uint32_t threshold_rank(Workspace& ws, const RankInfo& ri, float threshold, HostScratch& hs) {

@@ -727,6 +727,8 @@ void run_reduction(const ReduceIn& in, const ReduceOut& out, bool keep_zero, Wor
     e.clear_next = out.clear_next;
     e.counters = out.counters;
     e.keep_zero = keep_zero ? 1 : 0;
+    e.next_list = out.next_list;
+    e.next_len = out.next_len;
     switch (in.p) {
         case 1: run_p<1>(c, e, ws, hs); break;
         case 2: run_p<2>(c, e, ws, hs); break;

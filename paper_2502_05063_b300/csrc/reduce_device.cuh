@@ -380,6 +380,8 @@ struct Emit {
     uint32_t* clear_next;
     unsigned long long* counters;  // [0] additions [1] pairs [2] essential
     int keep_zero;
+    const uint64_t* next_list;     // sparse mode: clear_next by position in this sorted list (else NULL)
+    int64_t next_len;
 };
 
 // Record the finished column j with pivot key `key` (EMPTY = zero column).
@@ -401,7 +403,19 @@ __device__ void finish_column(const Ctx& c, const Emit& e, int64_t j, uint64_t k
     const uint32_t rt = (uint32_t)(key >> c.rcb);
     const uint64_t ct = c.rcmask - (key & c.rcmask);
     hash_insert(c, ct, (uint32_t)j);
-    if (e.clear_next) atomicOr(e.clear_next + (ct >> 5), 1u << (ct & 31));
+    if (e.clear_next) {
+        uint64_t bit = ct;
+        if (e.next_list) {  // position of ct among the listed (p+1)-simplices
+            int64_t lo = 0, hi = e.next_len;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (e.next_list[mid] < ct) lo = mid + 1; else hi = mid;
+            }
+            bit = (uint64_t)lo;
+            if (lo >= e.next_len) atomicExch(c.err, DEV_INTERNAL | (7 << 8));
+        }
+        if (!e.next_list || (int64_t)bit < e.next_len) atomicOr(e.clear_next + (bit >> 5), 1u << (bit & 31));
+    }
     atomicAdd(e.counters + 1, 1ull);
     if (rt > rs || e.keep_zero) {
         pr.death_rank = rt;

@@ -227,6 +227,7 @@ struct RankInfo {
 };
 RankInfo build_ranks(Workspace& ws, const float* lower_tri, int64_t n, HostScratch& hs);
 uint32_t threshold_rank(Workspace& ws, const RankInfo& ri, float threshold, HostScratch& hs);
+void clamp_ranks(Workspace& ws, const RankInfo& ri, int64_t n, uint32_t thr_rank);  // ranks > thr -> thr + 1
 
 // Device-side records of emitted pairs (ranks, not values).
 struct PairRec {
@@ -253,10 +254,34 @@ struct ApparentOut {
     unsigned long long* counters; // [0] above_threshold [1] cleared [2] columns [3] apparent
     int64_t capacity;             // capacity of nonapparent_keys
     int* dev_err;
+    // sparse mode: clear_next is indexed by position in this sorted list of the
+    // (p+1)-simplex indices of the complex (NULL: indexed by the index itself)
+    const uint64_t* next_list = nullptr;
+    int64_t next_len = 0;
 };
 void launch_filtration_apparent(int p, const RankMatrix& R, const Binom& B, uint32_t thr_rank,
                                 const uint32_t* clear_bits, int cidx_bits, int rank_bits, uint64_t num_cand,
                                 const ApparentOut& o, cudaStream_t s);
+
+// sparse.cu : the complex listed from neighbour lists (sparse / low-threshold mode).
+constexpr int SIMPLEX_VSTRIDE = 8;  // vertices stored per listed simplex (uint16, ascending, p+1 used)
+struct Neighbours {               // CSR lists of the threshold graph, ascending
+    uint32_t* off;                // n + 1
+    uint32_t* nbr;
+    int64_t num;
+};
+struct SimplexList {              // simplices of one dimension, by combinatorial index ascending
+    uint64_t* cidx;
+    uint16_t* verts;              // SIMPLEX_VSTRIDE per simplex
+    int64_t len;
+};
+Neighbours build_neighbours(Workspace& ws, const RankMatrix& R, uint32_t thr, HostScratch& hs);
+SimplexList edge_list(Workspace& ws, const RankMatrix& R, const Neighbours& N, HostScratch& hs);
+SimplexList next_list(Workspace& ws, const RankMatrix& R, const Binom& B, const Neighbours& N, uint32_t thr,
+                      const SimplexList& L, int p, int out_cidx_bits, HostScratch& hs);
+void launch_sparse_filtration_apparent(int p, const RankMatrix& R, const Binom& B, const Neighbours& N,
+                                       const SimplexList& L, const uint32_t* clear_bits, bool clear_by_pos,
+                                       int cidx_bits, int rank_bits, const ApparentOut& o, cudaStream_t s);
 
 // reduce.cu : Z/2 reduction of the non-apparent columns (Algorithm 12).
 struct ReduceIn {
@@ -275,6 +300,8 @@ struct ReduceOut {
     PairRec* pairs;               // capacity num_cols
     unsigned long long* num_pairs;
     uint32_t* clear_next;         // may be NULL
+    const uint64_t* next_list = nullptr;  // sparse mode: clear_next indexed by position in this list
+    int64_t next_len = 0;
     unsigned long long* counters; // [0] additions [1] pairs [2] essential
     int* dev_err;
 };

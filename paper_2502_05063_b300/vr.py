@@ -29,6 +29,7 @@ VR_DEBUG_CHECKS = 0x4
 VR_APPARENT_ONLY = 0x8
 VR_REDUCE_V = 0x10
 VR_REDUCE_OBLIVIOUS = 0x20
+VR_SPARSE = 0x40
 
 STATUS = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_OOM", 3: "VR_ERR_INDEX_OVERFLOW",
           4: "VR_ERR_CUDA", 5: "VR_ERR_TIMEOUT", 6: "VR_ERR_INTERNAL"}
