@@ -293,6 +293,75 @@ def reduction_ablation(stream, reps=3):
     return out
 
 
+def sparse_mode(stream, reps=3):
+    """The sparse (low-threshold) mode against the dense enumeration on the same
+    call: the O(3)-sample stand-in (n=4096 in R^9, threshold 1.4, 2.8% of the
+    pairs, H0-H2) and the 500-point torus at the 10th percentile of its
+    distances.  Median call time of `reps` calls (CUDA events, device-resident
+    input) after one warm-up, and per dimension the listed simplices and the
+    fused kernel's time."""
+    import numpy as np
+    import torch
+    from paper_2502_05063_b300 import synth, vr
+    out = {}
+    tor = synth.WORKLOADS["torus500"]["make"]()
+    dt = np.sort(np.linalg.norm(tor[:, None, :] - tor[None, :, :], axis=2)[np.tril_indices(500, -1)])
+    cases = {"o3like4096": (synth.WORKLOADS["o3like4096"]["make"](), 2, 1.4),
+             "torus500_q10": (tor, 2, float(dt[len(dt) // 10]))}
+    for name, (pts, dmax, thr) in cases.items():
+        x = torch.from_numpy(pts).cuda()
+        res = {"n": int(pts.shape[0]), "dmax": dmax, "threshold": thr}
+        for mode, fl in (("sparse", vr.VR_SPARSE), ("dense", 0)):
+            try:
+                vr.barcodes(points=x, dmax=dmax, threshold=thr, flags=fl, stream=stream)
+                runs = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = vr.barcodes(points=x, dmax=dmax, threshold=thr, flags=fl, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    runs.append((e0.elapsed_time(e1), r))
+                runs.sort(key=lambda t: t[0])
+                ms, r = runs[len(runs) // 2]
+                res[mode] = {"call_ms": ms, "dims": {"dim%d" % p: {k: r.stats[p][k] for k in (
+                    "candidates", "columns", "apparent", "reduced", "ms_filtration", "ms_reduce")}
+                    for p in range(1, dmax + 1)}, "bars": [len(a) for a in r.pairs]}
+            except Exception as e:  # noqa: BLE001
+                res[mode] = {"error": str(e)}
+        out[name] = res
+    return out
+
+
+def hypha_bench(stream, reps=5):
+    """HYPHA (Ch. 4) on the explicit boundary matrix of the lower-star
+    filtration of a 512 x 512 triangulated grid with random vertex values
+    (1,568,771 columns, 3,135,496 entries), device-resident input: the whole
+    call (median of `reps` after one warm-up), its phases (library stage
+    timers) and the GPU scan's rate in columns and entries per second."""
+    import torch
+    from paper_2502_05063_b300 import synth, vr
+    colptr, rows, _ = synth.lower_star_grid(512, seed=7)
+    cp, rw = torch.from_numpy(colptr).cuda(), torch.from_numpy(rows).cuda()
+    vr.hypha_pairs(cp, rw, stream=stream)
+    runs = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        low, st = vr.hypha_pairs(cp, rw, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        runs.append((e0.elapsed_time(e1), st))
+    runs.sort(key=lambda t: t[0])
+    ms, st = runs[len(runs) // 2]
+    ncol, nnz = len(colptr) - 1, len(rows)
+    return {"workload": "lower-star filtration of a 512x512 Freudenthal-triangulated grid, random vertex values, "
+                        "seed 7 (boundary matrix %d columns, %d entries)" % (ncol, nnz),
+            "call_ms": ms, "stats": st,
+            "scan_columns_per_s": ncol / (st["ms_scan"] / 1e3) if st["ms_scan"] > 0 else None,
+            "scan_entries_per_s": nnz / (st["ms_scan"] / 1e3) if st["ms_scan"] > 0 else None}
+
+
 RANDPERM_NS = (50, 100, 200, 400, 1000, 2000, 4000, 9000)
 
 
@@ -597,6 +666,8 @@ def run_ours(args):
         line["other_workloads"] = other_workload_rates(stream)
         line["randperm"] = randperm_curve(stream)
         line["reduction_ablation"] = reduction_ablation(stream)
+        line["sparse_mode"] = sparse_mode(stream)
+        line["hypha"] = hypha_bench(stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_single()
         if not args.no_batched:

@@ -286,6 +286,36 @@ vr_status vr_sort_u64(uint64_t* keys, uint64_t* values, int64_t num, int32_t bit
  * serialised by the caller.  Every call synchronises `stream` before it
  * returns (the sort is finished on return), so no call of it may be made
  * while `stream` is being captured into a CUDA graph.                       */
+/* Persistence pairs of an explicit boundary matrix: HYPHA (Ch. 4, Algorithm
+ * 10) -- the GPU scan for leftmost entries and 0-addition columns
+ * (Algorithms 3-6), clearing (Algorithm 7, Lemma 4.2.3), compression
+ * (Algorithms 8-9, Lemmas 4.2.4-4.2.5), then the standard reduction
+ * (Algorithm 2) of the columns that remain, all on the device.
+ *  colptr   int64[ncols+1], rows int32[nnz]: the Z/2 boundary matrix of a
+ *           filtered simplicial complex in CSC form, columns (and rows) in
+ *           filtration order, the rows of each column ascending and below
+ *           the column (faces come first); host or device memory.
+ *           Clearing and compression rely on it being a boundary matrix.
+ *  flags    must be 0.
+ *  out_low  int32[ncols], host or device: the pivot row of each column of
+ *           the fully reduced matrix (low(R_j)), -1 for a zero column; the
+ *           pairs (low(R_j), j) are the persistence pairs (Thm 3.2.20).
+ *  stats    may be NULL.
+ * A malformed matrix (rows out of order, a row not below its column)
+ * returns VR_ERR_INVALID_ARG.                                              */
+typedef struct {
+    int64_t columns;
+    int64_t unstable;               /* columns neither stable (0-addition) nor cleared     */
+    int64_t compression_passes;     /* fixed-point passes of the compressible-row search   */
+    int64_t compression_additions;  /* stable columns added during compression            */
+    int64_t additions;              /* column additions of the final reduction             */
+    float ms_scan;                  /* GPU scan and clearing                               */
+    float ms_compression;
+    float ms_reduce;
+} vr_hypha_stats;
+vr_status vr_hypha_pairs(const int64_t* colptr, const int32_t* rows, int64_t ncols, int64_t nnz, uint32_t flags,
+                         void* stream, int32_t* out_low, vr_hypha_stats* stats);
+
 /* Read-bandwidth probe for the roofline denominators (the paper has no
  * counterpart).  Streams a zeroed device buffer of `bytes` bytes `iters`
  * times with 16-byte loads that bypass L1, on `stream`, and writes the read

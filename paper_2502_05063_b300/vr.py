@@ -115,6 +115,7 @@ lib.vr_barcodes_batched_device.argtypes = [_vp, _vp, _i32, _i32, _i32, _f32, _u3
                                            ctypes.POINTER(ctypes.POINTER(BatchDeviceResult))]
 lib.vr_batch_device_result_free.argtypes = [ctypes.POINTER(BatchDeviceResult)]
 lib.vr_batch_device_result_free.restype = None
+lib.vr_hypha_pairs.argtypes = [_vp, _vp, _i64, _i64, _u32, _vp, _vp, _vp]
 lib.vr_probe_read_gbs.argtypes = [_i64, _i32, _vp, ctypes.POINTER(ctypes.c_double)]
 if hasattr(lib, "vr_barcodes_batched"):
     lib.vr_barcodes_batched.argtypes = [_vp, _vp, _i32, _i32, _i32, _f32, _u32, _vp,
@@ -390,3 +391,22 @@ def barcodes_batched_device(points, offsets, dmax=1, threshold=np.inf, flags=0, 
     finally:
         _copies_done()
         lib.vr_batch_device_result_free(out)
+
+
+class HyphaStats(ctypes.Structure):
+    _fields_ = [("columns", ctypes.c_int64), ("unstable", ctypes.c_int64), ("compression_passes", ctypes.c_int64),
+                ("compression_additions", ctypes.c_int64), ("additions", ctypes.c_int64),
+                ("ms_scan", ctypes.c_float), ("ms_compression", ctypes.c_float), ("ms_reduce", ctypes.c_float)]
+
+
+def hypha_pairs(colptr, rows, stream=None):
+    """low(R_j) of every column of an explicit boundary matrix (CSC, numpy or
+    torch, host or GPU): numpy int32 array, -1 for zero columns; and the stats."""
+    cp, keep_cp = _ptr_of(colptr)
+    rw, keep_rw = _ptr_of(rows)
+    n = int(colptr.shape[0]) - 1
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    st = HyphaStats()
+    _check(lib.vr_hypha_pairs(cp, rw, n, int(rows.shape[0]), 0, _stream_ptr(stream), out.ctypes.data,
+                              ctypes.byref(st)), "vr_hypha_pairs")
+    return out[:n], {f: getattr(st, f) for f, _ in HyphaStats._fields_}

@@ -83,3 +83,15 @@ def test_sparse_empty_and_edgeless(vr):
     assert len(bc.pairs[0]) == 50 and all(math.isinf(float(x)) for x in bc.pairs[0]["death"])
     assert len(bc.pairs[1]) == 0 and len(bc.pairs[2]) == 0
     assert bc.stats[1]["candidates"] == 0 and bc.stats[2]["candidates"] == 0
+
+
+def test_sparse_o3_sample(vr):
+    """The O(3)-sample stand-in at the paper's threshold 1.4, 600 points, H0-H2:
+    sparse, dense and the oracle agree."""
+    pts = synth.orthogonal_group(600, seed=16)
+    D = oracle.distances_f32(pts)
+    sp = vr.barcodes(points=pts, dmax=2, threshold=1.4, flags=vr.VR_SPARSE | vr.VR_DEBUG_CHECKS)
+    pairs, _ = oracle.cohom(D.astype(np.float64), 600, 2, float(np.float32(1.4)), clearing=True)
+    dg = oracle.diagram(pairs, 2)
+    for p in range(3):
+        assert rows(sp, p) == oracle_rows(dg[p]), p
