@@ -692,6 +692,19 @@ def run_single():
     return 0
 
 
+def run_single_batched(num):
+    """One batched call on the first `num` clouds of the 4096-cloud workload (for
+    profiler captures of the persistent kernel)."""
+    import torch
+    from paper_2502_05063_b300 import synth, vr
+    clouds, _ = synth.batch_clouds()
+    pts, offs = synth.pack(clouds[:num])
+    bb = vr.barcodes_batched(torch.from_numpy(pts).cuda(), offs, dmax=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"clouds": num, "pairs": [int(o[-1]) for o in bb.offsets]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -702,9 +715,13 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurements")
     ap.add_argument("--single", action="store_true",
                     help="one untimed call of the workload (for profiler captures), prints its stage counts")
+    ap.add_argument("--single-batched", type=int, default=0, metavar="N",
+                    help="one batched call on the first N clouds of the 4096-cloud workload (profiler captures)")
     args = ap.parse_args()
     if args.single:
         return run_single()
+    if args.single_batched:
+        return run_single_batched(args.single_batched)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
