@@ -609,6 +609,10 @@ static vr_result* compute(Workspace& ws, const float* lower, int64_t n, int dmax
         in.cols = keys;
         in.num_cols = nna;
         in.mode = (flags & VR_REDUCE_V) ? 1 : (flags & VR_REDUCE_OBLIVIOUS) ? 2 : 0;
+        if (sparse) {  // coboundaries from the neighbour lists
+            in.nb_off = nb.off;
+            in.nb = nb.nbr;
+        }
         ReduceOut out;
         out.pairs = pr;
         out.num_pairs = rc;

@@ -720,6 +720,8 @@ void run_reduction(const ReduceIn& in, const ReduceOut& out, bool keep_zero, Wor
     c.pool_used = ws.zeros_n<unsigned long long>(1);
     c.rc_ptr = ws.alloc_n<uint64_t>((size_t)in.num_cols);
     c.mode = in.mode;
+    c.nb_off = in.nb_off;
+    c.nb = in.nb;
     c.rc_len = ws.zeros_n<uint32_t>((size_t)in.num_cols);
     Emit e;
     e.pairs = out.pairs;

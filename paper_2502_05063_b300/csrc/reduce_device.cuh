@@ -41,6 +41,10 @@ struct Ctx {
     // (front and back), 1 = every column keeps V_j (generators) only,
     // 2 = oblivious (Algorithm 12 as printed: nothing is kept, owners add D_o)
     int mode;
+    // sparse mode (Sec. 5.3.12): CSR lists of the threshold graph, ascending;
+    // null: cofacets are enumerated over every vertex
+    const uint32_t* nb_off = nullptr;
+    const uint32_t* nb = nullptr;
 };
 constexpr int MODE_EXPLICIT = 0, MODE_V = 1, MODE_OBLIVIOUS = 2;
 
@@ -56,6 +60,32 @@ struct Simplex {
     uint32_t r;     // diameter rank
     uint64_t cidx;
 };
+
+// Candidate vertices w of the cofacets x + {w} of a simplex, largest first:
+// every vertex, or in sparse mode the neighbour list of x's vertex with the
+// fewest neighbours (Alg 15: a cofacet within the threshold is adjacent to
+// every vertex of x; the rank test made on each candidate excludes the rest).
+struct Cands {
+    const uint32_t* list;  // null: all vertices
+    int64_t cnt;
+    __device__ __forceinline__ int64_t operator[](int64_t i) const {  // the i-th largest, i < cnt
+        return list ? (int64_t)list[cnt - 1 - i] : cnt - 1 - i;
+    }
+};
+template <int P>
+__device__ __forceinline__ Cands cofacet_cands(const Ctx& c, const int* v) {
+    if (!c.nb_off) return Cands{nullptr, c.R.n};
+    uint32_t b = c.nb_off[v[0]], e = c.nb_off[v[0] + 1];
+#pragma unroll
+    for (int q = 1; q <= P; ++q) {
+        const uint32_t bq = c.nb_off[v[q]], eq = c.nb_off[v[q] + 1];
+        if (eq - bq < e - b) {
+            b = bq;
+            e = eq;
+        }
+    }
+    return Cands{c.nb + b, (int64_t)(e - b)};
+}
 
 template <int P>
 __device__ __forceinline__ void load_col(const Ctx& c, uint64_t key, Simplex<P>& s) {
@@ -123,13 +153,14 @@ constexpr int RC = 4;
 template <int P, int K = RC>
 __device__ void warp_rows_above(const Ctx& c, const Simplex<P>& x, bool has_cut, uint64_t cut, uint64_t* out) {
     const int lane = threadIdx.x & 31;
-    const int64_t n = c.R.n;
+    const Cands cw = cofacet_cands<P>(c, x.v);
     const uint32_t rcut = has_cut ? (uint32_t)(cut >> c.rcb) : 0u;
     uint64_t t[K];
 #pragma unroll
     for (int r = 0; r < K; ++r) t[r] = EMPTY;
-    for (int64_t base = n - 1; base >= 0; base -= 32) {
-        const int64_t w = base - lane;
+    for (int64_t i0 = 0; i0 < cw.cnt; i0 += 32) {
+        const int64_t i = i0 + lane;
+        const int64_t w = i < cw.cnt ? cw[i] : -1;
         bool ok = w >= 0;
 #pragma unroll
         for (int q = 0; q <= P; ++q) ok = ok && (w != x.v[q]);
@@ -225,8 +256,10 @@ __device__ bool warp_owner(const Ctx& c, uint64_t rk, uint64_t self_key, Simplex
     for (int q = 0; q < NT; ++q)
         if (q != drop) o.v[k++] = tv[q];
     const int64_t wd = tv[drop];
-    for (int64_t base = n - 1; base > wd; base -= 32) {
-        const int64_t w = base - lane;
+    const Cands cw = cofacet_cands<P>(c, o.v);
+    for (int64_t i0 = 0; i0 < cw.cnt && cw[i0] > wd; i0 += 32) {  // largest first: stop below wd
+        const int64_t i = i0 + lane;
+        const int64_t w = i < cw.cnt ? cw[i] : -1;
         bool ok = w > wd;
 #pragma unroll
         for (int q = 0; q <= P; ++q) ok = ok && (w != o.v[q]);
@@ -1147,20 +1180,22 @@ __device__ __forceinline__ bool cob_row(const Ctx& c, const Simplex<P>& x, int64
 }
 
 // W <- W + D_x for the p-simplex x (vertices ascending, diameter rank x.r),
-// HT vertices w per pass from the top.
+// HT candidate vertices w per pass, largest first, from the first-th.
 template <int P>
 __device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x,
-                                     int64_t top) {
-    for (int64_t base = top; base >= 0; base -= HT) {
+                                     int64_t first) {
+    const Cands cw = cofacet_cands<P>(c, x.v);
+    for (int64_t i0 = first; i0 < cw.cnt; i0 += HT) {
+        const int64_t i = i0 + threadIdx.x;
         uint64_t key = EMPTY;
-        const bool ok = cob_row<P>(c, x, base - (int64_t)threadIdx.x, key);
+        const bool ok = cob_row<P>(c, x, i < cw.cnt ? cw[i] : -1, key);
         if (!heavy_cob_place(S, B, bcap, ok, key)) return false;
     }
     return true;
 }
 template <int P>
 __device__ bool heavy_add_coboundary(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, const Simplex<P>& x) {
-    return heavy_add_coboundary<P>(c, S, B, bcap, x, c.R.n - 1);
+    return heavy_add_coboundary<P>(c, S, B, bcap, x, 0);
 }
 
 // Sort stage[0..cnt) (cnt <= HSTAGE), keep one row of every run of odd
@@ -1205,9 +1240,11 @@ __device__ bool heavy_add_stored(const Ctx& c, HeavySmem& S, uint64_t* B, int64_
     for (int64_t i = 0; i < len; ++i) {
         Simplex<P> g;
         load_col<P>(c, gk[i], g);
-        for (int64_t base = c.R.n - 1; base >= 0; base -= HT) {
+        const Cands cw = cofacet_cands<P>(c, g.v);
+        for (int64_t i0 = 0; i0 < cw.cnt; i0 += HT) {
+            const int64_t iw = i0 + threadIdx.x;
             uint64_t key = EMPTY;
-            const bool ok = cob_row<P>(c, g, base - (int64_t)threadIdx.x, key);
+            const bool ok = cob_row<P>(c, g, iw < cw.cnt ? cw[iw] : -1, key);
             const bool lt = ok && key < S.Ks, ge = ok && !lt;
             int tot;
             const int packed = block_excl_scan((int)lt | ((int)ge << 16), S.ws, &tot);
@@ -1386,15 +1423,16 @@ __device__ int heavy_owner_probe(const Ctx& c, HeavySmem& S, uint64_t rk, uint64
 // above the dropped one keeps the diameter of s' (s' has no older cofacet).
 template <int P>
 __device__ bool heavy_apparent_check(const Ctx& c, HeavySmem& S) {
-    const int64_t n = c.R.n;
     int ov[P + 1];
 #pragma unroll
     for (int q = 0; q <= P; ++q) ov[q] = S.ov[q];
     const int64_t wd = S.ov[P + 1];
     const uint32_t rt = S.orank;
+    const Cands cw = cofacet_cands<P>(c, ov);
     bool older = false;
-    for (int64_t base = n - 1; base > wd; base -= HT) {
-        const int64_t w = base - (int64_t)threadIdx.x;
+    for (int64_t i0 = 0; i0 < cw.cnt && cw[i0] > wd; i0 += HT) {  // largest first: stop below wd
+        const int64_t i = i0 + (int64_t)threadIdx.x;
+        const int64_t w = i < cw.cnt ? cw[i] : -1;
         bool ok = w > wd;
 #pragma unroll
         for (int q = 0; q <= P; ++q) ok = ok && (w != ov[q]);
@@ -1416,18 +1454,18 @@ template <int P, bool OVERLAP = true>
 __device__ int heavy_apparent_add(const Ctx& c, HeavySmem& S, uint64_t* B, int64_t bcap, uint64_t self_key,
                                   int* next_kind) {
     *next_kind = 0;
-    const int64_t n = c.R.n;
     Simplex<P> o;
 #pragma unroll
     for (int q = 0; q <= P; ++q) o.v[q] = S.ov[q];
     o.r = S.orank;
     const int64_t wd = S.ov[P + 1];
-    if (wd < n - 1 - HT) {
+    const Cands cw = cofacet_cands<P>(c, o.v);
+    if (cw.cnt > HT && cw[HT] > wd) {  // the first pass does not reach every candidate above wd
         if (!heavy_apparent_check<P>(c, S)) return -1;
         return heavy_add_coboundary<P>(c, S, B, bcap, o) ? 1 : 0;
     }
     HPROF_T0();
-    const int64_t w = n - 1 - (int64_t)threadIdx.x;
+    const int64_t w = (int64_t)threadIdx.x < cw.cnt ? cw[threadIdx.x] : -1;
     bool ok = w >= 0, older = false;
 #pragma unroll
     for (int q = 0; q <= P; ++q) ok = ok && (w != o.v[q]);
@@ -1443,10 +1481,10 @@ __device__ int heavy_apparent_add(const Ctx& c, HeavySmem& S, uint64_t* B, int64
     }
     if (__syncthreads_or(older)) return -1;
     HPROF_LAP(14);
-    if (OVERLAP && n <= HT)  // this was the only pass: probe the next pivot's owner during the merge
+    if (OVERLAP && cw.cnt <= HT)  // this was the only pass: probe the next pivot's owner during the merge
         return heavy_cob_place_next<P>(c, S, B, bcap, ok, key, self_key, next_kind) ? 1 : 0;
     if (!heavy_cob_place(S, B, bcap, ok, key)) return 0;
-    return heavy_add_coboundary<P>(c, S, B, bcap, o, n - 1 - HT) ? 1 : 0;
+    return heavy_add_coboundary<P>(c, S, B, bcap, o, HT) ? 1 : 0;
 }
 
 }  // namespace

@@ -295,6 +295,8 @@ struct ReduceIn {
     const uint64_t* cols; // sorted column keys, num_cols
     int64_t num_cols;
     int mode;             // 0: explicit reduced columns, 1: V (generators), 2: oblivious (Sec. 5.2.9)
+    const uint32_t* nb_off = nullptr;  // sparse mode: the threshold graph's CSR lists (cofacets from them)
+    const uint32_t* nb = nullptr;
 };
 struct ReduceOut {
     PairRec* pairs;               // capacity num_cols
