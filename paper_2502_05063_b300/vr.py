@@ -296,11 +296,14 @@ class _DevArray:
                                          "version": 3, "strides": None}
 
 
-def _copies_done():
-    """The copies out of a device result were queued on torch's current stream,
-    the result is freed in the order of the call's stream: let them finish."""
+def _copies_done(stream):
+    """The copies out of a device result were queued on torch's current stream
+    and the library frees the result in the order of the call's stream: on the
+    same stream the free follows the copies; on another, let them finish."""
     import torch
-    torch.cuda.current_stream().synchronize()
+    cur = torch.cuda.current_stream()
+    if (_stream_ptr(stream) or 0) != cur.cuda_stream:
+        cur.synchronize()
 
 
 def _own(ptr, count, per, torch_dtype, cols):
@@ -355,7 +358,7 @@ def barcodes_device(points=None, dists=None, n=None, dmax=1, threshold=np.inf, f
     try:
         return DeviceBarcodes(out.contents)
     finally:
-        _copies_done()
+        _copies_done(stream)
         lib.vr_device_result_free(out)
 
 
@@ -389,7 +392,7 @@ def barcodes_batched_device(points, offsets, dmax=1, threshold=np.inf, flags=0, 
     try:
         return DeviceBatchBarcodes(out.contents)
     finally:
-        _copies_done()
+        _copies_done(stream)
         lib.vr_batch_device_result_free(out)
 
 
