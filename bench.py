@@ -634,6 +634,19 @@ def run_ours(args):
         except (OSError, ValueError):
             traffic = None
 
+    # The step's dominant kernel is the block engine's reduction (k_reduce_heavy):
+    # a chain of dependent column additions, bound by their latency, not by a
+    # bandwidth or an issue rate; its share of the step and time per addition.
+    red_ms = sum(stage["dim%d" % p]["ms_reduce"] for p in range(1, dmax + 1))
+    dominant = {"kernel": "k_reduce_heavy<1..%d> (with the warp-engine round)" % dmax,
+                "bound": "latency of dependent additions",
+                "share_of_step": red_ms / (total_ms / args.steps),
+                "per_dimension": {"dim%d" % p: {"ms_reduce": stage["dim%d" % p]["ms_reduce"],
+                                                "additions": last.stats[p]["additions"],
+                                                "us_per_addition": 1000 * stage["dim%d" % p]["ms_reduce"]
+                                                / max(last.stats[p]["additions"], 1)}
+                                  for p in range(1, dmax + 1)},
+                "profile": "profiles/reduce_heavy_torus500.md, profiles/launches_torus500.md"}
     stage_rates = stage_rates_of(last.stats, dmax, stage)
     stage_rates["note"] = "dimensions 1-%d; filtration and apparent search run as one fused kernel" % dmax
 
@@ -654,7 +667,8 @@ def run_ours(args):
                      "peak_source": "hbm_gbs of MEASURED_PEAKS.json (%s; burst copy)" % peak_src,
                      "l2": {"peak": probes["l2_read_gbs"], "frac": achieved / probes["l2_read_gbs"],
                             "peak_source": "project L2-resident read probe, this run"},
-                     "target_frac": 0.5},
+                     "target_frac": 0.5,
+                     "dominant": dominant},
         "peaks_probe": probes,
         "issue": issue,
         "stages_ms": stage,
