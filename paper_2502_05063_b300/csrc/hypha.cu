@@ -207,120 +207,314 @@ __global__ void k_apply_compression(const int64_t* __restrict__ cp, const int32_
     }
 }
 
-// Final phase: Algorithm 2 on the unstable columns in order, one block.
-// Columns are read from the compressed scratch (out_len >= 0) or the input,
-// with compressible rows dropped; reduced columns are appended to `pool`.
+// Final phase: Algorithm 2 on the unstable columns in order, by one warp.
+// A row travels with the first column index from which it is droppable
+// (droppable(r, j) <=> j >= t), so dropping needs no further lookup; the
+// owner of a pivot row, and where its reduced column lives (the input rows of
+// a stable column, or the pool for a column reduced here), is one 16-byte
+// record.  Each addition: read the owner record of the working column's low,
+// load the owner's rows that column j keeps (one coalesced pass, ballot
+// compaction), and merge them into the working column by warp merge path.
+struct __align__(8) RowT {
+    int32_t r;  // row
+    int32_t t;  // the row is droppable for columns j >= t (INF32: never)
+};
+constexpr int OWN_IN = 4;  // rows kept in the record itself (input columns of dimension <= 2 have at most 3)
+struct __align__(16) Owner {
+    int64_t off;  // of its rows in `rows_t` or, with POOL_BIT, in `pool`
+    int32_t len;
+    int32_t col;  // the owning column, -1: none
+    RowT in[OWN_IN];  // its rows when len <= OWN_IN: one read per addition
+};
+constexpr int64_t POOL_BIT = (int64_t)1 << 62;
+
+__global__ void k_drop_from(const uint8_t* __restrict__ C, const int32_t* __restrict__ lk0, int64_t n,
+                            int32_t* __restrict__ T) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        T[r] = C[r] != C_YES ? INF32 : (lk0[r] < 0 ? 0 : lk0[r] + 1);  // as droppable(), reading L < 0 || L < j
+}
+
+__global__ void k_rows_t(const int32_t* __restrict__ rows, int64_t nnz, const int32_t* __restrict__ T,
+                         RowT* __restrict__ rows_t) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        rows_t[e] = RowT{rows[e], T[rows[e]]};
+}
+
+// owner records of the pivots the scan found (stable columns)
+__global__ void k_owner_init(const int64_t* __restrict__ cp, int64_t n, const int32_t* __restrict__ lk0,
+                             const RowT* __restrict__ rows_t, Owner* __restrict__ own) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = lk0[r];
+        Owner w{};
+        w.col = -1;
+        if (o >= 0) {
+            w.off = cp[o];
+            w.len = (int32_t)(cp[o + 1] - cp[o]);
+            w.col = o;
+            if (w.len <= OWN_IN)
+                for (int i = 0; i < w.len; ++i) w.in[i] = rows_t[w.off + i];
+        }
+        own[r] = w;
+    }
+}
+
+// out <- a XOR b for ascending rows without repeats, by one warp; returns the
+// length.  Lane L starts at diagonal L * per of the merged sequence (equal rows:
+// a's first, and a boundary between equal rows moves before them, so a
+// cancelling pair is never split); a first walk counts each lane's cancelling
+// pairs, a warp scan turns the counts into output offsets, a second walk writes.
+__device__ int warp_xor_merge(const RowT* a, int la, const RowT* b, int lb, RowT* out) {
+    const int lane = threadIdx.x & 31;
+    const int tot = la + lb;
+    const int per = (tot + 31) >> 5;
+    const int d = min(tot, lane * per);
+    int lo = max(0, d - la), hi = min(d, lb);  // b rows among the first d: largest k with b[k-1] < a[d-k]
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (b[m - 1].r < a[d - m].r) lo = m;
+        else hi = m - 1;
+    }
+    const int k0 = lo;
+    int i0 = d - lo;
+    if (i0 > 0 && k0 < lb && a[i0 - 1].r == b[k0].r) --i0;
+    int i1 = __shfl_down_sync(0xffffffffu, i0, 1), k1 = __shfl_down_sync(0xffffffffu, k0, 1);
+    if (lane == 31) {
+        i1 = la;
+        k1 = lb;
+    }
+    int c = 0;
+    for (int i = i0, k = k0; i < i1 && k < k1;) {
+        const int32_t x = a[i].r, y = b[k].r;
+        c += x == y;
+        i += x <= y;
+        k += y <= x;
+    }
+    int cs = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, cs, o);
+        if (lane >= o) cs += t;
+    }
+    const int ctot = __shfl_sync(0xffffffffu, cs, 31);
+    int pos = i0 + k0 - 2 * (cs - c);
+    for (int i = i0, k = k0; i < i1 || k < k1;) {
+        const int32_t x = i < i1 ? a[i].r : INF32, y = k < k1 ? b[k].r : INF32;
+        if (x == y) {
+            ++i;
+            ++k;
+        } else if (x < y) {
+            out[pos++] = a[i++];
+        } else {
+            out[pos++] = b[k++];
+        }
+    }
+    __syncwarp();
+    return tot - 2 * ctot;
+}
+
+// rows of src[0..len) that column j keeps, appended in order at dst[at..); returns the new end
+__device__ __forceinline__ int warp_keep(const RowT* src, int64_t len, int32_t j, RowT* dst, int at) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t e0 = 0; e0 < len; e0 += 32) {
+        const int64_t e = e0 + lane;
+        RowT x{INF32, 0};
+        bool keep = false;
+        if (e < len) {
+            x = src[e];
+            keep = j < x.t;
+        }
+        const unsigned bl = __ballot_sync(0xffffffffu, keep);
+        if (keep) dst[at + __popc(bl & ((1u << lane) - 1u))] = x;
+        at += __popc(bl);
+    }
+    return at;
+}
+
 struct FinalArgs {
     const int64_t* cp;
-    const int32_t* rows;
+    const RowT* rows_t;  // the input rows with their drop thresholds
+    const int32_t* T;
     const int32_t* u;
     int64_t nu;
-    const int32_t* scratch;
+    const int32_t* scratch;  // compressed slots, converted to RowT pairs (k_slot_rows_t)
     int64_t cap;
     const int32_t* clen;
-    const uint8_t* C;
-    const int32_t* lk0;  // pivots of the stable columns (the scan's lookup)
-    int32_t* lookup;     // updated with the new pivots
-    int64_t* red_off;    // per unstable column: offset of its reduced rows in pool (-1: zero)
-    int32_t* red_len;
-    int32_t* upos;       // column -> position in u (-1 if not unstable)
-    int32_t* pool;
+    Owner* own;          // per row: the owner of that pivot, updated with the new pivots
+    RowT* pool;
     int64_t pool_cap;
-    int32_t* work;       // two working buffers of work_cap rows
+    RowT* work;          // three working buffers of work_cap rows
     int64_t work_cap;
     int32_t* low_out;    // n
     unsigned long long* adds;
     int* err;
 };
 
-constexpr int FT = 32;
+// In place: the compressed rows of each slot (int32) become RowT pairs, from
+// the last one down (pair e covers the int32 entries 2e and 2e+1, all read by then).
+__global__ void k_slot_rows_t(int32_t* __restrict__ scratch, int64_t cap, const int32_t* __restrict__ clen,
+                              int64_t nu, const int32_t* __restrict__ T) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nu; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t len = clen[q];
+        int32_t* col = scratch + q * 2 * cap;
+        RowT* out = reinterpret_cast<RowT*>(col);
+        for (int32_t e = len - 1; e >= 0; --e) {
+            const int32_t r = col[e];
+            out[e] = RowT{r, T[r]};
+        }
+    }
+}
 
+constexpr int FT = 32;
+constexpr int FS = 4096;  // rows of each shared working buffer (the global ones take longer columns)
+
+// where the rows of unstable column q are: its compressed slot, or its input rows
+struct ColSrc {
+    const RowT* src;
+    int64_t len;
+};
+__device__ __forceinline__ ColSrc col_src(const FinalArgs& A, int64_t q, int32_t clen, int64_t a, int64_t b) {
+    if (clen >= 0) return ColSrc{reinterpret_cast<const RowT*>(A.scratch + q * 2 * A.cap), clen};
+    return ColSrc{A.rows_t + a, b - a};
+}
+
+// The unstable columns in order.  Their inputs do not depend on the reduction,
+// so they are fetched ahead in three stages that never wait on one another:
+// while column q is reduced, the first 32 rows of column q+1, the offsets of
+// column q+2 and the index of column q+3 are in flight.
 __global__ void __launch_bounds__(FT, 1) k_final_reduce(FinalArgs A) {
-    __shared__ int64_t s_len;
-    __shared__ int s_flag;
-    int32_t* w0 = A.work;
-    int32_t* w1 = A.work + A.work_cap;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    RowT* sw = reinterpret_cast<RowT*>(fsm);  // three buffers of FS rows
+    const int lane = threadIdx.x & 31;
+    const int64_t nu = A.nu;
     unsigned long long adds = 0;
     int64_t pool_used = 0;
-    for (int64_t q = 0; q < A.nu; ++q) {
-        const int32_t j = A.u[q];
-        // load column j, compressible rows dropped (one thread: order matters)
-        if (threadIdx.x == 0) {
-            int64_t len = 0;
-            const bool comp = A.clen[q] >= 0;
-            const int32_t* src = comp ? A.scratch + q * 2 * A.cap : A.rows + A.cp[j];
-            const int64_t sl = comp ? A.clen[q] : A.cp[j + 1] - A.cp[j];
-            for (int64_t e = 0; e < sl; ++e) {
-                const int32_t r = src[e];
-                if (!droppable(A.C, A.lk0, r, j)) w0[len++] = r;
-            }
-            s_len = len;
-            s_flag = 0;
+    const RowT none{INF32, 0};
+    // prime the pipeline
+    int32_t j0 = A.u[0], c0 = A.clen[0];
+    ColSrc s0 = col_src(A, 0, c0, c0 < 0 ? A.cp[j0] : 0, c0 < 0 ? A.cp[j0 + 1] : 0);
+    RowT r0 = lane < s0.len ? s0.src[lane] : none;
+    int32_t j1 = -1, c1 = 0;
+    int64_t a1 = 0, b1 = 0;
+    if (nu > 1) {
+        j1 = A.u[1];
+        c1 = A.clen[1];
+        if (c1 < 0) {
+            a1 = A.cp[j1];
+            b1 = A.cp[j1 + 1];
         }
-        __syncthreads();
+    }
+    int32_t j2 = -1, c2 = 0;
+    if (nu > 2) {
+        j2 = A.u[2];
+        c2 = A.clen[2];
+    }
+    for (int64_t q = 0; q < nu; ++q) {
+        // stage loads for the next three columns (consumed in later iterations)
+        int32_t j3 = -1, c3 = 0;
+        if (q + 3 < nu) {
+            j3 = A.u[q + 3];
+            c3 = A.clen[q + 3];
+        }
+        int64_t a2 = 0, b2 = 0;
+        if (q + 2 < nu && c2 < 0) {
+            a2 = A.cp[j2];
+            b2 = A.cp[j2 + 1];
+        }
+        ColSrc s1{nullptr, 0};
+        RowT r1 = none;
+        if (q + 1 < nu) {
+            s1 = col_src(A, q + 1, c1, a1, b1);
+            if (lane < s1.len) r1 = s1.src[lane];
+        }
+        // reduce column q
+        const int32_t j = j0;
+        if (s0.len > A.work_cap) {
+            if (lane == 0) atomicExch(A.err, DEV_CAPACITY);
+            return;
+        }
+        bool big = s0.len > FS;  // the working column and the owner's kept rows in shared memory while they fit
+        RowT* w0 = big ? A.work : sw;
+        RowT* w1 = big ? A.work + A.work_cap : sw + FS;
+        RowT* wb = big ? A.work + 2 * A.work_cap : sw + 2 * FS;
+        int len;
+        {
+            const bool keep = lane < s0.len && j < r0.t;
+            const unsigned bl = __ballot_sync(0xffffffffu, keep);
+            if (keep) w0[__popc(bl & ((1u << lane) - 1u))] = r0;
+            len = __popc(bl);
+            if (s0.len > 32) len = warp_keep(s0.src + 32, s0.len - 32, j, w0, len);
+        }
+        __syncwarp();
         for (;;) {
-            const int64_t len = s_len;
             if (len == 0) break;
-            const int32_t low = w0[len - 1];
-            const int32_t o = A.lookup[low];
-            if (o < 0 || o >= j) break;  // the pivot is new: j is reduced
-            // the owner's reduced column: a stable column (its input rows) or a
-            // reduced unstable one (in the pool)
-            const int32_t* osrc;
-            int64_t olen;
-            const int32_t op = A.upos[o];
-            if (op >= 0) {
-                osrc = A.pool + A.red_off[op];
-                olen = A.red_len[op];
-            } else {
-                osrc = A.rows + A.cp[o];
-                olen = A.cp[o + 1] - A.cp[o];
-            }
-            if (len + olen > A.work_cap) {
-                if (threadIdx.x == 0) atomicExch(A.err, DEV_CAPACITY);
+            const int32_t low = w0[len - 1].r;
+            const Owner ow = A.own[low];
+            if (ow.col < 0 || ow.col >= j) break;  // the pivot is new: j is reduced
+            if ((int64_t)len + ow.len > A.work_cap) {
+                if (lane == 0) atomicExch(A.err, DEV_CAPACITY);
                 return;
             }
-            // XOR merge (compressible rows of the owner dropped as read)
-            if (threadIdx.x == 0) {
-                int64_t i = 0, k = 0, w = 0;
-                while (i < len || k < olen) {
-                    const int32_t y = k < olen ? osrc[k] : INF32;
-                    if (k < olen && droppable(A.C, A.lk0, y, j)) { ++k; continue; }
-                    const int32_t x = i < len ? w0[i] : INF32;
-                    if (x == y) { ++i; ++k; continue; }
-                    if (x < y) { w1[w++] = x; ++i; }
-                    else { w1[w++] = y; ++k; }
-                }
-                s_len = w;
+            if (!big && len + ow.len > FS) {  // move to the global buffers
+                for (int e = lane; e < len; e += 32) A.work[e] = w0[e];
+                __syncwarp();
+                big = true;
+                w0 = A.work;
+                w1 = A.work + A.work_cap;
+                wb = A.work + 2 * A.work_cap;
             }
-            __syncthreads();
-            int32_t* t = w0; w0 = w1; w1 = t;
+            int lb;
+            if (ow.len <= OWN_IN) {  // the rows came with the record
+                RowT x = none;
+#pragma unroll
+                for (int i = 0; i < OWN_IN; ++i)
+                    if (lane == i && i < ow.len) x = ow.in[i];
+                const bool keep = lane < ow.len && j < x.t;
+                const unsigned bl = __ballot_sync(0xffffffffu, keep);
+                if (keep) wb[__popc(bl & ((1u << lane) - 1u))] = x;
+                lb = __popc(bl);
+            } else {
+                const RowT* osrc = (ow.off & POOL_BIT) ? A.pool + (ow.off & ~POOL_BIT) : A.rows_t + ow.off;
+                lb = warp_keep(osrc, ow.len, j, wb, 0);
+            }
+            __syncwarp();
+            len = warp_xor_merge(w0, len, wb, lb, w1);
+            RowT* t = w0;
+            w0 = w1;
+            w1 = t;
             ++adds;
         }
-        if (threadIdx.x == 0) {
-            const int64_t len = s_len;
-            if (len > 0) {
-                const int32_t low = w0[len - 1];
-                A.lookup[low] = j;
-                A.low_out[j] = low;
-                if (pool_used + len > A.pool_cap) {
-                    atomicExch(A.err, DEV_CAPACITY);
-                    s_flag = 1;
-                } else {
-                    for (int64_t e = 0; e < len; ++e) A.pool[pool_used + e] = w0[e];
-                    A.red_off[q] = pool_used;
-                    A.red_len[q] = (int32_t)len;
-                    pool_used += len;
-                }
-            } else {
-                A.red_off[q] = 0;
-                A.red_len[q] = 0;
+        if (len > 0) {
+            if (pool_used + len > A.pool_cap) {
+                if (lane == 0) atomicExch(A.err, DEV_CAPACITY);
+                return;
             }
+            for (int e = lane; e < len; e += 32) A.pool[pool_used + e] = w0[e];
+            const int32_t low = w0[len - 1].r;
+            if (lane == 0) {
+                Owner w{};
+                w.off = pool_used | POOL_BIT;
+                w.len = len;
+                w.col = j;
+                if (len <= OWN_IN)
+                    for (int i = 0; i < len; ++i) w.in[i] = w0[i];
+                A.own[low] = w;
+                A.low_out[j] = low;
+            }
+            pool_used += len;
         }
-        __syncthreads();
-        if (s_flag) return;
+        __syncwarp();
+        // advance the pipeline
+        j0 = j1;
+        s0 = s1;
+        r0 = r1;
+        j1 = j2;
+        c1 = c2;
+        a1 = a2;
+        b1 = b2;
+        j2 = j3;
+        c2 = c3;
     }
-    if (threadIdx.x == 0) atomicAdd(A.adds, adds);
+    if (lane == 0) atomicAdd(A.adds, adds);
 }
 
 // lows of the stable nonzero columns (their input lows are final)
@@ -333,10 +527,6 @@ __global__ void k_stable_lows(const int64_t* __restrict__ cp, const int32_t* __r
     }
 }
 
-__global__ void k_upos(const int32_t* __restrict__ u, int64_t nu, int32_t* __restrict__ upos) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nu; q += (int64_t)gridDim.x * blockDim.x)
-        upos[u[q]] = (int32_t)q;
-}
 
 __global__ void k_check_rows(const int64_t* __restrict__ cp, const int32_t* __restrict__ rows, int64_t n,
                              int* __restrict__ err) {
@@ -455,23 +645,27 @@ extern "C" vr_status vr_hypha_pairs(const int64_t* colptr, const int32_t* rows, 
         // ---- final reduction of the unstable columns
         int32_t* low_d = ws.alloc_n<int32_t>(n);
         k_stable_lows<<<hgrid(n), 256, 0, s>>>(cp, rw, n, stable, cleared, lookup, low_d);
-        int32_t* upos = ws.alloc_n<int32_t>(n);
-        VR_CUDA(cudaMemsetAsync(upos, 0xFF, n * sizeof(int32_t), s));
         if (nu > 0) {
-            k_upos<<<hgrid(nu), 256, 0, s>>>(u, nu, upos);
+            int32_t* T = ws.alloc_n<int32_t>(n);
+            RowT* rows_t = ws.alloc_n<RowT>(std::max<int64_t>(nnz, 1));
+            Owner* own = ws.alloc_n<Owner>(n);
+            k_drop_from<<<hgrid(n), 256, 0, s>>>(C, lk0, n, T);
+            k_rows_t<<<hgrid(nnz), 256, 0, s>>>(rw, nnz, T, rows_t);
+            k_owner_init<<<hgrid(n), 256, 0, s>>>(cp, n, lk0, rows_t, own);
+            k_slot_rows_t<<<hgrid(nu), 256, 0, s>>>(scratch, cap, clen, nu, T);
             FinalArgs A;
-            A.cp = cp; A.rows = rw; A.u = u; A.nu = nu; A.scratch = scratch; A.cap = cap; A.clen = clen;
-            A.C = C; A.lk0 = lk0; A.lookup = lookup; A.upos = upos;
-            A.red_off = ws.alloc_n<int64_t>(nu);
-            A.red_len = ws.alloc_n<int32_t>(nu);
+            A.cp = cp; A.rows_t = rows_t; A.T = T; A.u = u; A.nu = nu; A.scratch = scratch; A.cap = cap;
+            A.clen = clen; A.own = own;
             A.pool_cap = std::max<int64_t>(nnz * 8, 1 << 20);
-            A.pool = ws.alloc_n<int32_t>(A.pool_cap);
+            A.pool = ws.alloc_n<RowT>(A.pool_cap);
             A.work_cap = std::max<int64_t>(n, 1 << 16);
-            A.work = ws.alloc_n<int32_t>(2 * A.work_cap);
+            A.work = ws.alloc_n<RowT>(3 * A.work_cap);
             A.low_out = low_d;
             A.adds = ctr + 3;
             A.err = err;
-            k_final_reduce<<<1, FT, 0, s>>>(A);
+            const size_t fsmem = 3 * FS * sizeof(RowT);
+            VR_CUDA(cudaFuncSetAttribute(k_final_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+            k_final_reduce<<<1, FT, fsmem, s>>>(A);
             VR_CUDA(cudaGetLastError());
         }
         tm.mark();
