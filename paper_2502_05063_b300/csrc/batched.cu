@@ -569,8 +569,11 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
                         ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, o);
                     }
                 } else {
-                    // small clouds: the plain merge (the overlapped probe does not pay here)
-                    const int r = heavy_apparent_add<1, false>(c, S, back, BACKCAP, self_key, &pre);
+                    // the next pivot's owner is probed during the merge (one pass covers
+                    // n <= 256): 85.4 -> 80.8 ms on the 4096-cloud batch, 5.55 -> 5.22 ms
+                    // on the 256 circles, where one long cocycle column per cloud holds
+                    // nearly all the additions
+                    const int r = heavy_apparent_add<1, true>(c, S, back, BACKCAP, self_key, &pre);
                     if (r < 0) break;  // the pivot has no owner: the column is complete
                     ok = r > 0;
                 }
