@@ -33,6 +33,7 @@
 //    of the columns before it) and runs as one small block on the device, each
 //    addition a merge of sorted rows.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -344,6 +345,7 @@ struct FinalArgs {
     int64_t pool_cap;
     RowT* work;          // three working buffers of work_cap rows
     int64_t work_cap;
+    int fs;              // rows the shared buffers take (FS; lowered by VR_HYPHA_SHARED_ROWS for tests)
     int32_t* low_out;    // n
     unsigned long long* adds;
     int* err;
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(FT, 1) k_final_reduce(FinalArgs A) {
             if (lane == 0) atomicExch(A.err, DEV_CAPACITY);
             return;
         }
-        bool big = s0.len > FS;  // the working column and the owner's kept rows in shared memory while they fit
+        bool big = s0.len > A.fs;  // the working column and the owner's kept rows in shared memory while they fit
         RowT* w0 = big ? A.work : sw;
         RowT* w1 = big ? A.work + A.work_cap : sw + FS;
         RowT* wb = big ? A.work + 2 * A.work_cap : sw + 2 * FS;
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(FT, 1) k_final_reduce(FinalArgs A) {
                 if (lane == 0) atomicExch(A.err, DEV_CAPACITY);
                 return;
             }
-            if (!big && len + ow.len > FS) {  // move to the global buffers
+            if (!big && len + ow.len > A.fs) {  // move to the global buffers
                 for (int e = lane; e < len; e += 32) A.work[e] = w0[e];
                 __syncwarp();
                 big = true;
@@ -663,6 +665,8 @@ extern "C" vr_status vr_hypha_pairs(const int64_t* colptr, const int32_t* rows, 
             A.low_out = low_d;
             A.adds = ctr + 3;
             A.err = err;
+            A.fs = FS;
+            if (const char* v = getenv("VR_HYPHA_SHARED_ROWS")) A.fs = (int)std::min<long>(FS, std::max(1L, atol(v)));
             const size_t fsmem = 3 * FS * sizeof(RowT);
             VR_CUDA(cudaFuncSetAttribute(k_final_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
             k_final_reduce<<<1, FT, fsmem, s>>>(A);

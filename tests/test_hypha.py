@@ -143,3 +143,20 @@ def test_hypha_rejects_malformed(vr):
     rows = np.array([1, 0], np.int32)  # rows not ascending
     with pytest.raises(vr.VRError):
         vr.hypha_pairs(colptr, rows)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shared_rows", [1, 4, 64])
+def test_hypha_global_working_buffers(vr, shared_rows, monkeypatch):
+    """The final phase keeps the working column in shared memory while it fits
+    (4096 rows) and moves to global buffers past that; lowering the limit
+    (read on each call) sends the same reductions through the global path."""
+    monkeypatch.setenv("VR_HYPHA_SHARED_ROWS", str(shared_rows))
+    for m, seed in [(10, 3), (40, 4)]:
+        colptr, rows, _ = synth.lower_star_grid(m, seed=seed)
+        low, _ = vr.hypha_pairs(colptr, rows)
+        assert low.tolist() == oracle.reduce_explicit(csc_columns(colptr, rows)).tolist()
+    for n, top, seed in [(14, 3, 2), (25, 2, 5)]:
+        colptr, rows, _ = rips_boundary(n, top, seed)
+        low, _ = vr.hypha_pairs(colptr, rows)
+        assert low.tolist() == oracle.reduce_explicit(csc_columns(colptr, rows)).tolist()
