@@ -334,7 +334,6 @@ __device__ __forceinline__ int warp_keep(const RowT* src, int64_t len, int32_t j
 struct FinalArgs {
     const int64_t* cp;
     const RowT* rows_t;  // the input rows with their drop thresholds
-    const int32_t* T;
     const int32_t* u;
     int64_t nu;
     const int32_t* scratch;  // compressed slots, converted to RowT pairs (k_slot_rows_t)
@@ -656,7 +655,7 @@ extern "C" vr_status vr_hypha_pairs(const int64_t* colptr, const int32_t* rows, 
             k_owner_init<<<hgrid(n), 256, 0, s>>>(cp, n, lk0, rows_t, own);
             k_slot_rows_t<<<hgrid(nu), 256, 0, s>>>(scratch, cap, clen, nu, T);
             FinalArgs A;
-            A.cp = cp; A.rows_t = rows_t; A.T = T; A.u = u; A.nu = nu; A.scratch = scratch; A.cap = cap;
+            A.cp = cp; A.rows_t = rows_t; A.u = u; A.nu = nu; A.scratch = scratch; A.cap = cap;
             A.clen = clen; A.own = own;
             A.pool_cap = std::max<int64_t>(nnz * 8, 1 << 20);
             A.pool = ws.alloc_n<RowT>(A.pool_cap);

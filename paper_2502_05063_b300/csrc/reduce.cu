@@ -237,6 +237,21 @@ __device__ void heavy_column(const Ctx& c, const uint32_t* __restrict__ U, int64
     __syncthreads();
     const int64_t slot = slot_sh;
     if (slot < 0) return;
+    if (hs.init[slot] && status[j] == ST_COMPLETE) {
+        // complete in an earlier round and waiting to be finalized in order: it
+        // changes only if its pivot has since become a finished column's pivot
+        // (whether it has an apparent owner never changes), so one probe of the
+        // hash stands in for reloading and saving its state
+        __shared__ int still;
+        const uint64_t key = cur_key[j];
+        if (key == EMPTY) return;  // a zero column stays zero
+        if (threadIdx.x < 32) {
+            const int64_t hp = warp_hash_find(c, c.rcmask - (key & c.rcmask));
+            if (threadIdx.x == 0) still = hp < 0;
+        }
+        __syncthreads();
+        if (still) return;
+    }
     uint64_t* B = hs.B[slot];
     const int64_t bcap = hs.bcap[slot];
     const uint64_t self_key = c.cols[j];
