@@ -598,6 +598,9 @@ __device__ void block_bitonic(uint64_t* a, int len) {
 // upper half of the stage, which costs one barrier instead of the log^2
 // barrier stages of a bitonic network; more rows are sorted in place by the
 // bitonic network.
+// DISTINCT: the rows are known to differ (one pass of one coboundary), so a
+// row's rank needs no tie-break.
+template <bool DISTINCT = false>
 __device__ const uint64_t* stage_sort(HeavySmem& S, int cnt) {
     if (cnt <= 1) return S.stage;
     if (cnt <= HT && cnt <= HSTAGE / 2) {
@@ -605,9 +608,14 @@ __device__ const uint64_t* stage_sort(HeavySmem& S, int cnt) {
         if (i < cnt) {
             const uint64_t x = S.stage[i];
             int rank = 0;
-            for (int j = 0; j < cnt; ++j) {
-                const uint64_t y = S.stage[j];
-                rank += (y < x) || (y == x && j < i);
+            if (DISTINCT) {
+#pragma unroll 8
+                for (int j = 0; j < cnt; ++j) rank += S.stage[j] < x;
+            } else {
+                for (int j = 0; j < cnt; ++j) {
+                    const uint64_t y = S.stage[j];
+                    rank += (y < x) || (y == x && j < i);
+                }
             }
             S.stage[HSTAGE / 2 + rank] = x;
         }
@@ -1056,7 +1064,7 @@ __device__ bool heavy_cob_place(HeavySmem& S, uint64_t* B, int64_t bcap, bool ok
     }
     __syncthreads();
     HPROF_LAP(0);
-    const uint64_t* srt = stage_sort(S, nlt);
+    const uint64_t* srt = stage_sort<true>(S, nlt);
     HPROF_LAP(1);
     if (!heavy_merge_front(S, B, bcap, srt, nlt)) return false;
     HPROF_LAP(2);
@@ -1099,7 +1107,7 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
     }
     __syncthreads();
     HPROF_LAP(0);
-    const uint64_t* srt = stage_sort(S, nlt);
+    const uint64_t* srt = stage_sort<true>(S, nlt);
     HPROF_LAP(1);
     *next_kind = 0;
     if (nlt == 0) return true;
