@@ -1148,8 +1148,12 @@ __device__ bool heavy_cob_place_next(const Ctx& c, HeavySmem& S, uint64_t* B, in
             }
             const bool fs = f != EMPTY && !(qf < fr && run[qf] == f);
             const bool rs = r != EMPTY && !(qr < fa && F[qr] == r);
-            const uint64_t mine = fs ? (rs && r < f ? r : f) : (rs ? r : EMPTY);
-            pn = warp_min_u64(mine);
+            // both heads ascend with the lane: each one's smallest survivor is
+            // its first surviving lane
+            const unsigned bf = __ballot_sync(0xffffffffu, fs), br = __ballot_sync(0xffffffffu, rs);
+            const uint64_t f0 = __shfl_sync(0xffffffffu, f, bf ? __ffs(bf) - 1 : 0);
+            const uint64_t r0 = __shfl_sync(0xffffffffu, r, br ? __ffs(br) - 1 : 0);
+            pn = bf ? (br && r0 < f0 ? r0 : f0) : (br ? r0 : EMPTY);
             const uint64_t f32 = a > 32 ? F[32] : EMPTY, r32 = nlt > 32 ? run[32] : EMPTY;
             certain = pn < (f32 < r32 ? f32 : r32);
             if (lane == 0) { S.sel = certain ? pn : EMPTY; }
