@@ -22,6 +22,7 @@
 // A cloud that outgrows a per-block buffer is flagged and recomputed by the
 // host through the single-cloud path.
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -89,7 +90,7 @@ struct BatchArgs {
 };
 
 struct BatchSmem {
-    HeavySmem S;
+    HeavySmem S;  // first: the bitmap engine addresses its arena from the start of shared memory
     float pts[BMAXN * BMAXDIM];
     uint32_t clear[(BMAXN * (BMAXN - 1) / 2 + 31) / 32];
     uint64_t tree[BMAXN];
@@ -106,6 +107,8 @@ struct BatchSmem {
     uint64_t wmin[HW];
     int wcnt[HW];
 };
+static_assert(offsetof(BatchSmem, S) == 0, "the engine arena starts the shared memory");
+
 
 __device__ __forceinline__ void edge_of(int e, int& a, int& b) {
     int x = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
@@ -177,6 +180,567 @@ __device__ void emit_block(const BatchArgs& A, BatchSmem& M, int p, int cloud, c
         }
     }
     __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// 5c. The bitmap engine (dimension 1, n <= 256).  A cloud's working column
+// W is one bit per triangle, at the triangle's index (eq. 5.6, below 2^22),
+// so W <- W + D_s flips the bits of the cofacets of s and nothing is sorted
+// or merged.  The pivot of W is its smallest row in coboundary order: the
+// smallest diameter, then the largest index.  Rows are bucketed by the
+// dense rank of their diameter among the distinct distances within the
+// threshold; a triangle of diameter rank r holds an edge of rank r, so the
+// rows of bucket r are found among the triangles {a, b, w} over the edges
+// (a, b) of rank r (one edge unless distances tie) and the third vertices
+// w.  One bit per bucket marks those that may hold a row (every warp finds
+// the lowest by a minimum over the words): a bucket's bit is set whenever
+// one of its rows flips, and cleared when its search finds nothing or when
+// the rows of the last pivot's bucket, counted, run out.
+// Owners follow the block engine's rule: the pivot of a finished column
+// (hash), else the apparent owner of Def 5.3.4 recomputed; a finished
+// column is added as its reduced form, the sum of the coboundaries of the
+// generators it records (its column of V).
+// Three variants by the cloud's size (bit_variant): the bitmap, the bucket
+// starts and the ranks in shared memory (n <= 128); the ranks only (n <=
+// 172); neither.  The head, the bucket bits and the edges by distance are
+// always in shared memory, the rest in the slot's global scratch.
+// Shared data are addressed from the dynamic shared array itself, so the
+// accesses compile to shared-space instructions.
+// ---------------------------------------------------------------------------
+extern __shared__ __align__(16) unsigned char g_bsm[];
+
+constexpr int BIT_VCAP = 1 << 16;  // generators of the column being reduced
+// per-slot global scratch carved from `back` (in 8-byte units)
+constexpr int64_t BIT_KEYS = 0;                                                // sort keys, 32768
+constexpr int64_t BIT_RK = BIT_KEYS + 32768;                                   // u16 dense ranks
+constexpr int64_t BIT_G = BIT_RK + 8192;                                       // u16 bucket starts
+constexpr int64_t BIT_ES = BIT_G + 8200;                                       // u16 edges by distance
+constexpr int64_t BIT_BITS = BIT_ES + 8192;                                    // u32 bitmap, C(256,3) bits
+constexpr int64_t BIT_V = BIT_BITS + ((int64_t)BMAXN * (BMAXN - 1) * (BMAXN - 2) / 6 + 63) / 64;
+static_assert(BIT_V + BIT_VCAP <= BACKCAP, "the bitmap engine's scratch fits the back buffer");
+static_assert(BMAXN * (BMAXN - 1) / 2 < 0xFFFF, "dense ranks fit 16 bits below the above-threshold mark");
+
+struct BitHead {
+    uint32_t best[3];         // pivot search results, (index << 8) | w, the largest wins; used in rotation
+    int cnt[3];               // rows found by the same searches (a tie may count a row twice)
+    int dcnt;                 // rows of the last pivot's bucket the last addition set (+1) or cleared (-1)
+    int opos;                 // position of the finished column owning the pivot, or -1
+    int fail;
+    unsigned long long poff;  // where the finished column's generators go in the pool
+    int ws[HW + 1];
+};
+
+struct BitEng {
+    uint32_t o_h0, o_G, o_Es, o_bits, o_rk;  // byte offsets in the dynamic shared memory
+    const uint16_t* gG;   // [nR + 1]: bucket r holds the edges Es[G[r] .. G[r+1])
+    const uint16_t* gEs;  // edges within the threshold by distance, as (a << 8) | b, a > b
+    uint32_t* gbits;      // the working column, [nbw] words
+    const uint16_t* grk;  // dense rank per edge index, 0xFFFF above the threshold
+    uint64_t* vbuf;       // generators of the current column (edge indices)
+    int n, nbw, nR;
+    bool ident;           // every bucket holds one edge (no two distances tie): bucket r is Es[r]
+};
+
+__device__ __forceinline__ BitHead& bit_hd() { return *reinterpret_cast<BitHead*>(g_bsm); }
+__device__ __forceinline__ uint32_t* bit_h0(const BitEng& E) { return reinterpret_cast<uint32_t*>(g_bsm + E.o_h0); }
+// SB: the bitmap and the bucket starts in shared memory (n <= 128); SR: the
+// ranks too (n <= 172).  The edges by distance always are.
+template <bool SB>
+__device__ __forceinline__ const uint16_t* bit_G(const BitEng& E) {
+    if constexpr (SB) return reinterpret_cast<const uint16_t*>(g_bsm + E.o_G); else return E.gG;
+}
+__device__ __forceinline__ const uint16_t* bit_Es(const BitEng& E) {
+    return reinterpret_cast<const uint16_t*>(g_bsm + E.o_Es);
+}
+template <bool SR>
+__device__ __forceinline__ const uint16_t* bit_rk(const BitEng& E) {
+    if constexpr (SR) return reinterpret_cast<const uint16_t*>(g_bsm + E.o_rk); else return E.grk;
+}
+template <bool SB>
+__device__ __forceinline__ uint32_t* bit_bits(const BitEng& E) {
+    if constexpr (SB) return reinterpret_cast<uint32_t*>(g_bsm + E.o_bits); else return E.gbits;
+}
+// a word of W after a barrier: shared memory as is, global past the L1 (flipped by atomics)
+template <bool SB>
+__device__ __forceinline__ uint32_t bit_word(const BitEng& E, uint32_t i) {
+    if constexpr (SB) return bit_bits<true>(E)[i]; else return __ldcg(E.gbits + i);
+}
+
+__device__ __forceinline__ uint32_t bit_eidx(uint32_t u, uint32_t v) {  // u != v
+    const uint32_t x = u > v ? u : v, y = u > v ? v : u;
+    return x * (x - 1) / 2 + y;
+}
+
+// index of the triangle {u, v, w} (distinct vertices), eq. 5.6
+__device__ __forceinline__ uint32_t bit_tidx(uint32_t u, uint32_t v, uint32_t w) {
+    const uint32_t x0 = min(u, min(v, w)), x2 = max(u, max(v, w)), x1 = u + v + w - x0 - x2;
+    return x2 * (x2 - 1) * (x2 - 2) / 6 + x1 * (x1 - 1) / 2 + x0;
+}
+
+// Clear bucket r's bit; every thread may do it at once (the same value is written).
+__device__ __forceinline__ void bit_clear_bucket(const BitEng& E, int r) {
+    uint32_t* h0 = bit_h0(E);
+    h0[r >> 5] = h0[r >> 5] & ~(1u << (r & 31));
+}
+
+// Flip row `t` (bucket d) of W if `on`; every lane of the warp calls this.
+// Rows of the last pivot's bucket rp (many rows of the added coboundary
+// lie at its diameter) leave its bit alone (set, and cleared only by the
+// count) and count whether they were set or cleared, summed per warp.
+// (Combining the other buckets' bits per warp first, lanes grouped by
+// target word, measured slower: 765 -> 3.8 K cycles per addition.)
+template <bool SB, bool SR>
+__device__ __forceinline__ void bit_flip(const BitEng& E, bool on, uint32_t t, uint32_t d, int rp) {
+    int delta = 0;
+    if (on) {
+        const uint32_t m = 1u << (t & 31);
+        uint32_t* w = bit_bits<SB>(E) + (t >> 5);
+        if ((int)d == rp) {
+            delta = (atomicXor(w, m) & m) ? -1 : 1;
+        } else {
+            atomicXor(w, m);
+            atomicOr(bit_h0(E) + (d >> 5), 1u << (d & 31));
+        }
+    }
+    if (rp >= 0) {
+        const int sum = __reduce_add_sync(0xffffffffu, delta);
+        if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&bit_hd().dcnt, sum);
+    }
+}
+
+// The row of D_s for the edge s = (u, v) of rank rs and this thread's
+// vertex w (none if w < 0): flipped if its diameter is within the threshold.
+template <bool SB, bool SR>
+__device__ __forceinline__ void bit_cob(const BitEng& E, int u, int v, uint32_t rs, int w, int rp) {
+    bool on = false;
+    uint32_t t = 0, d = 0;
+    if (w >= 0 && w != u && w != v) {
+        const uint16_t* rk = bit_rk<SR>(E);
+        const uint32_t mx = max(rs, max((uint32_t)rk[bit_eidx(u, w)], (uint32_t)rk[bit_eidx(v, w)]));
+        on = mx != 0xFFFFu;
+        d = mx;
+        t = bit_tidx(u, v, w);
+    }
+    bit_flip<SB, SR>(E, on, t, d, rp);
+}
+
+// W <- W + sum of D_g over the generators g (edge indices) in list[0..len),
+// two generators per pass (n <= 256 vertices each).
+template <bool SB, bool SR>
+__device__ void bit_add_list(const BitEng& E, const uint64_t* list, int len, int rp) {
+    for (int base = 0; base < len; base += HT / BMAXN) {
+        const int gi = base + (int)(threadIdx.x / BMAXN);
+        const int w = (int)(threadIdx.x % BMAXN);
+        int u = 0, v = 0;
+        uint32_t rs = 0;
+        const bool ok = gi < len && w < E.n;
+        if (ok) {
+            const int e = (int)list[gi];
+            edge_of(e, u, v);
+            rs = bit_rk<SR>(E)[e];
+        }
+        bit_cob<SB, SR>(E, u, v, rs, ok ? w : -1, rp);
+    }
+}
+
+// The pivot of W: false if W is zero, else the triangle {a, b, w} (a > b an
+// edge of bucket r) with the largest index among the rows of the lowest
+// non-empty bucket r.  rp, cp: the previous pivot's bucket (-1: none) and
+// the rows its search found; with the rows the last addition set or
+// cleared there (H.dcnt) they tell whether it emptied, in which case its
+// bit is cleared first.  Every warp finds the lowest set bucket bit itself
+// (a warp minimum over the words, no barrier); a bucket whose search finds
+// nothing is cleared and the next one searched.  `it` counts the searches
+// of the column: the result slot of search i is i mod 3, and slot i + 2 is
+// zeroed after search i's barrier, when search i - 1's slot has been read.
+template <bool SB, bool SR>
+__device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, uint32_t& a_out, uint32_t& b_out,
+                          uint32_t& w_out, uint32_t& t_out, int& c_out) {
+    BitHead& H = bit_hd();
+    const uint16_t* G = bit_G<SB>(E);
+    const uint16_t* Es = bit_Es(E);
+    const uint16_t* rk = bit_rk<SR>(E);
+    const uint32_t* h0 = bit_h0(E);
+    const int lane = threadIdx.x & 31;
+    const int nw = (E.nR + 31) >> 5;
+    if (rp >= 0 && cp + H.dcnt <= 0) bit_clear_bucket(E, rp);
+    for (;;) {
+        // the lowest non-empty word: eight words per lane loaded at once, lane
+        // i taking words i, i + 32, ...; a batch with a set bit ends the search
+        uint32_t lw = 0xFFFFFFFFu;
+        for (int base = 0; base < nw; base += 256) {
+            uint32_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = base + u * 32 + lane;
+                v[u] = i < nw ? h0[i] : 0u;
+            }
+#pragma unroll
+            for (int u = 7; u >= 0; --u)
+                if (v[u]) lw = (uint32_t)(base + u * 32 + lane);
+            if (__any_sync(0xffffffffu, lw != 0xFFFFFFFFu)) break;
+        }
+        lw = __reduce_min_sync(0xffffffffu, lw);
+        if (lw == 0xFFFFFFFFu) return false;
+        const int r = (int)(lw * 32 + __ffs(h0[lw]) - 1);
+        const int g0 = E.ident ? r : (int)G[r], k = E.ident ? 1 : (int)G[r + 1] - g0;
+        const uint32_t ab0 = Es[g0];  // the bucket's first (usually only) edge
+        const int sl = it % 3;
+        int found = 0;
+        for (int idx = threadIdx.x; idx < k * E.n; idx += HT) {
+            const int ei = k == 1 ? 0 : idx / E.n, w = idx - ei * E.n;
+            const uint32_t ab = ei == 0 ? ab0 : Es[g0 + ei], a = ab >> 8, b = ab & 0xFFu;
+            if (w == (int)a || w == (int)b) continue;
+            const uint32_t t = bit_tidx(a, b, w);
+            const uint32_t word = bit_word<SB>(E, t >> 5), ra = rk[bit_eidx(a, w)], rb = rk[bit_eidx(b, w)];
+            if (!((word >> (t & 31)) & 1u) || ra > (uint32_t)r || rb > (uint32_t)r) continue;  // absent, or another bucket's
+            ++found;
+            atomicMax(&H.best[sl], (t << 8) | (uint32_t)w);
+        }
+        if (found) atomicAdd(&H.cnt[sl], found);
+        __syncthreads();
+        const uint32_t best = H.best[sl];
+        const int cnt = H.cnt[sl];
+        if (threadIdx.x == 0) { H.best[(it + 2) % 3] = 0; H.cnt[(it + 2) % 3] = 0; }
+        ++it;
+        if (cnt) {
+            const uint32_t t = best >> 8, w = best & 0xFFu;
+            uint32_t a = ab0 >> 8, b = ab0 & 0xFFu;
+            for (int ei = 1; ei < k && !(a != w && b != w && bit_tidx(a, b, w) == t); ++ei) {  // ties only
+                a = Es[g0 + ei] >> 8;
+                b = Es[g0 + ei] & 0xFFu;
+            }
+            r_out = r; t_out = t; w_out = w; a_out = a; b_out = b; c_out = cnt;
+            if (threadIdx.x == 0) H.dcnt = 0;  // counted from the caller's next barrier on
+            return true;
+        }
+        bit_clear_bucket(E, r);  // bucket r is empty
+    }
+}
+
+// Which variant a cloud of n points takes, for the worst case (every edge
+// within the threshold, all distances distinct): 0 = SB and SR (head,
+// bucket bits, bucket starts, edges by distance and bitmap in the arena, the
+// sort keys there first, the ranks in the second arena), 1 = SR only, 2 =
+// neither (the edges by distance still in the arena).
+__device__ __forceinline__ int bit_variant(int n, size_t arena_bytes, size_t arena2_bytes) {
+    const size_t ne = (size_t)n * (n - 1) / 2, ntri = (size_t)n * (n - 1) * (n - 2) / 6;
+    const size_t hb = (sizeof(BitHead) + 15) & ~(size_t)15;
+    size_t lmax = 1;
+    while (lmax < ne) lmax <<= 1;
+    const size_t h0b = ((ne + 31) / 32 * 4 + 15) & ~(size_t)15;
+    const size_t gb = ((ne + 1) * 2 + 15) & ~(size_t)15, eb = (ne * 2 + 15) & ~(size_t)15;
+    const size_t bb = ((ntri + 31) / 32 * 4 + 15) & ~(size_t)15;
+    const bool sr = ne * 2 <= arena2_bytes;
+    if (sr && hb + lmax * 8 <= arena_bytes && hb + h0b + gb + eb + bb <= arena_bytes) return 0;
+    return sr ? 1 : 2;
+}
+
+// Per cloud: dense ranks of the edges within the threshold (a sort by
+// distance), the buckets, and the engine's storage (see bit_variant).
+template <bool SB, bool SR>
+__device__ BitEng bit_setup(uint64_t* back, const uint32_t* mat, int n, uint32_t thr, uint32_t arena2_off) {
+    BitEng E;
+    BitHead& H = bit_hd();
+    E.n = n;
+    E.vbuf = back + BIT_V;
+    uint16_t* Gg = reinterpret_cast<uint16_t*>(back + BIT_G);
+    uint16_t* Esg = reinterpret_cast<uint16_t*>(back + BIT_ES);
+    const int ne = n * (n - 1) / 2;
+    const uint32_t hb = (sizeof(BitHead) + 15) & ~15u;
+    uint64_t* keys = SB ? reinterpret_cast<uint64_t*>(g_bsm + hb) : back + BIT_KEYS;
+    uint16_t* rk;
+    if constexpr (SR) {
+        rk = reinterpret_cast<uint16_t*>(g_bsm + arena2_off);
+        E.o_rk = arena2_off;
+    } else {
+        rk = reinterpret_cast<uint16_t*>(back + BIT_RK);
+    }
+    E.grk = reinterpret_cast<const uint16_t*>(back + BIT_RK);
+    // 1. the edges within the threshold, as (distance bits << 16) | edge, in
+    // any order (they are sorted next); four distances in flight per thread
+    if (threadIdx.x == 0) H.cnt[0] = 0;  // the append counter (search slots are zeroed per column)
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < ne; base += 4 * HT) {
+        uint32_t d[4];
+        int e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            e[u] = base + u * HT + (int)threadIdx.x;
+            d[u] = 0xFFFFFFFFu;
+            if (e[u] < ne) {
+                int a, b;
+                edge_of(e[u], a, b);
+                d[u] = mat[a * BLD + b];
+                rk[e[u]] = 0xFFFFu;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool keep = e[u] < ne && d[u] <= thr;
+            const uint32_t bl = __ballot_sync(0xffffffffu, keep);
+            int at = 0;
+            if (lane == 0 && bl) at = atomicAdd(&H.cnt[0], __popc(bl));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (keep) keys[at + __popc(bl & ((1u << lane) - 1u))] = ((uint64_t)d[u] << 16) | (uint64_t)e[u];
+        }
+    }
+    __syncthreads();
+    const int m = H.cnt[0];
+    int len = 1;
+    while (len < m) len <<= 1;
+    for (int i = m + (int)threadIdx.x; i < len; i += HT) keys[i] = EMPTY;
+    __syncthreads();
+    block_bitonic(keys, len);
+    // 2. buckets: runs of equal distance
+    int nR = 0;
+    for (int base = 0; base < m; base += HT) {
+        const int p = base + (int)threadIdx.x;
+        bool first = false;
+        int e = 0;
+        if (p < m) {
+            const uint64_t k = keys[p];
+            e = (int)(k & 0xFFFFu);
+            first = p == 0 || (keys[p - 1] >> 16) != (k >> 16);
+        }
+        int tot;
+        const int pos = block_excl_scan(first, H.ws, &tot);
+        if (p < m) {
+            const int g = nR + pos + (first ? 0 : -1);
+            int a, b;
+            edge_of(e, a, b);
+            rk[e] = (uint16_t)g;
+            Esg[p] = (uint16_t)((a << 8) | b);
+            if (first) Gg[g] = (uint16_t)p;
+        }
+        nR += tot;
+    }
+    if (threadIdx.x == 0) Gg[nR] = (uint16_t)m;
+    E.nR = nR;
+    E.ident = nR == m;
+    const int64_t ntri = (int64_t)n * (n - 1) * (n - 2) / 6;
+    E.nbw = (int)((ntri + 31) / 32);
+    __syncthreads();
+    // 3. storage: bucket bits after the head (the keys are done with), then
+    // the edges by distance, then (SB) the bucket starts and the bitmap
+    uint32_t off = hb;
+    E.o_h0 = off;
+    off += (((uint32_t)(nR + 31) / 32) * 4 + 15) & ~15u;
+    E.gG = Gg;
+    E.gbits = reinterpret_cast<uint32_t*>(back + BIT_BITS);
+    const int ev = (m + 7) / 8;  // 16-byte vectors of 8 entries
+    E.o_Es = off;
+    off += (uint32_t)ev * 16;
+    uint4* es = reinterpret_cast<uint4*>(g_bsm + E.o_Es);
+    for (int i = threadIdx.x; i < ev; i += HT) es[i] = reinterpret_cast<const uint4*>(Esg)[i];
+    const int nbv = (E.nbw + 3) / 4;  // bitmap words in 16-byte vectors
+    if constexpr (SB) {
+        const int gv = (nR + 1 + 7) / 8;
+        E.o_G = off;
+        off += (uint32_t)gv * 16;
+        E.o_bits = off;
+        uint4* gs = reinterpret_cast<uint4*>(g_bsm + E.o_G);
+        for (int i = threadIdx.x; i < gv; i += HT) gs[i] = reinterpret_cast<const uint4*>(Gg)[i];
+        uint4* bw = reinterpret_cast<uint4*>(g_bsm + E.o_bits);
+        for (int i = threadIdx.x; i < nbv; i += HT) bw[i] = make_uint4(0, 0, 0, 0);
+    } else {
+        uint4* bw = reinterpret_cast<uint4*>(E.gbits);
+        for (int i = threadIdx.x; i < nbv; i += HT) bw[i] = make_uint4(0, 0, 0, 0);
+    }
+    uint32_t* h0 = bit_h0(E);
+    for (int i = threadIdx.x; i < (nR + 31) / 32; i += HT) h0[i] = 0;
+    if (threadIdx.x == 0) H.fail = 0;
+    __syncthreads();
+    return E;
+}
+
+// Reduce column j (position in cols) to completion on an empty W; returns
+// its pivot as a row key ((distance bits << TRI_BITS) | (mask - index)), or
+// EMPTY for a zero column.  `adds` receives the additions made and `vl` the
+// generators recorded in E.vbuf (R_j = D_j + sum of their D_g).  Sets
+// H.fail when a buffer is too small (the cloud is then recomputed by the
+// single-cloud path).  All threads take the same branches (vl, adds and
+// the owner are the same in every thread).
+template <bool SB, bool SR>
+__device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* mat, int j, unsigned long long& adds,
+                               int& vl) {
+    BitHead& H = bit_hd();
+    const uint16_t* rk = bit_rk<SR>(E);
+    const uint64_t self_key = c.cols[j];
+    const int ej = (int)(self_key & c.cmask);
+    const uint32_t rj = rk[ej];
+    int ja, jb;
+    edge_of(ej, ja, jb);
+    const int x = (int)threadIdx.x;  // this thread's third vertex
+    bit_cob<SB, SR>(E, ja, jb, rj, x < E.n ? x : -1, -1);
+    if (threadIdx.x < 3) { H.best[threadIdx.x] = 0; H.cnt[threadIdx.x] = 0; }
+    __syncthreads();
+    uint64_t key = EMPTY;
+    adds = 0;
+    vl = 0;
+    int it = 0, rp = -1, cp = 0;
+    for (;;) {
+        int r, cf;
+        uint32_t a, b, w, t;
+        if (!bit_pivot<SB, SR>(E, rp, cp, it, r, a, b, w, t, cf)) break;
+        rp = r;
+        cp = cf;
+        // warp 15 (no vertex of its own) probes the hash of finished columns;
+        // meanwhile every thread finds the candidate apparent owner s' (the
+        // facet left by dropping the largest vertex whose opposite edge keeps
+        // the diameter; w's is (a, b)) and tests its own cofacet of s'
+        if (threadIdx.x >= HT - 32) {
+            const int64_t hp = warp_hash_find(c, t);
+            if (threadIdx.x == HT - 32) H.opos = (int)hp;
+        }
+        const uint32_t ra = rk[bit_eidx(a, w)], rb = rk[bit_eidx(b, w)];
+        uint32_t wd = w;
+        if (rb == (uint32_t)r && a > wd) wd = a;
+        if (ra == (uint32_t)r && b > wd) wd = b;
+        const uint32_t su = wd == a ? b : a, sv = wd == w ? b : w;  // s' = {a, b, w} - {wd}
+        bool row = false, older = false;
+        uint32_t rt = 0, d = 0;
+        if (x < E.n && x != (int)su && x != (int)sv) {
+            const uint32_t mx = max((uint32_t)rk[bit_eidx(su, x)], (uint32_t)rk[bit_eidx(sv, x)]);
+            older = (uint32_t)x > wd && mx <= (uint32_t)r;  // s' + {x} is an older cofacet of s'
+            d = max((uint32_t)r, mx);
+            row = d != 0xFFFFu;
+            rt = bit_tidx(su, sv, x);
+        }
+        const int any_older = __syncthreads_or(older);
+        const int opos = H.opos;
+        if (opos < 0 && any_older) {  // the pivot has no owner: the column is complete
+            key = ((uint64_t)mat[a * BLD + b] << TRI_BITS) | (c.rcmask - t);
+            break;
+        }
+        if (adds >= (1ull << 22)) {  // far beyond any column of n <= 256
+            if (threadIdx.x == 0) H.fail = 1;
+            break;
+        }
+        ++adds;
+        if (opos >= 0) {
+            // the pivot of the finished column opos: add its reduced form
+            const uint32_t len = c.rc_len[opos];
+            const uint64_t* lst = reinterpret_cast<const uint64_t*>(c.rc_ptr[opos]);
+            const uint64_t eo = c.cols[opos] & c.cmask;
+            const int add = len ? (int)len : 1;
+            if (vl + add > BIT_VCAP) {
+                if (threadIdx.x == 0) H.fail = 1;
+                break;
+            }
+            if (len) {
+                bit_add_list<SB, SR>(E, lst, (int)len, r);
+                for (int i = threadIdx.x; i < (int)len; i += HT) E.vbuf[vl + i] = lst[i];
+            } else {
+                int oa, ob;
+                edge_of((int)eo, oa, ob);
+                bit_cob<SB, SR>(E, oa, ob, rk[eo], x < E.n ? x : -1, r);
+                if (threadIdx.x == 0) E.vbuf[vl] = eo;
+            }
+            vl += add;
+        } else {
+            // the apparent owner s', which precedes column j in coboundary order
+            // (larger distance, or equal distance and smaller index)
+            const uint32_t es = bit_eidx(su, sv);
+            if (threadIdx.x == 0 && !((uint32_t)r > rj || ((uint32_t)r == rj && (int)es < ej)))
+                atomicExch(c.err, DEV_INTERNAL | (5 << 8));
+            if (vl + 1 > BIT_VCAP) {
+                if (threadIdx.x == 0) H.fail = 1;
+                break;
+            }
+            bit_flip<SB, SR>(E, row, rt, d, r);
+            if (threadIdx.x == 0) E.vbuf[vl] = es;
+            vl += 1;
+        }
+        __syncthreads();
+    }
+    __syncthreads();  // H.fail is read by every thread after the return
+    return key;
+}
+
+// Empty W after column j (generators vbuf[0..vl)): a few coboundaries are
+// flipped back, a longer record is cheaper to wipe; the bucket bits are reset.
+template <bool SB, bool SR>
+__device__ void bit_clear(const BitEng& E, int ej, int vl) {
+    __syncthreads();
+    if (!SB && vl < 8) {
+        int ja, jb;
+        edge_of(ej, ja, jb);
+        const int x = (int)threadIdx.x;
+        bit_cob<SB, SR>(E, ja, jb, bit_rk<SR>(E)[ej], x < E.n ? x : -1, -1);
+        bit_add_list<SB, SR>(E, E.vbuf, vl, -1);
+    } else {
+        uint4* bw = reinterpret_cast<uint4*>(bit_bits<SB>(E));
+        for (int i = threadIdx.x; i < (E.nbw + 3) / 4; i += HT) bw[i] = make_uint4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    uint32_t* h0 = bit_h0(E);
+    for (int i = threadIdx.x; i < (E.nR + 31) / 32; i += HT) h0[i] = 0;
+    __syncthreads();
+}
+
+// 5c for one cloud: the columns ucur[0..nu) in order, each reduced to
+// completion; pairs appended to h1tmp (count *nh1), the pivots to the hash.
+// The hash moves to the second arena's free part when it fits.  Returns
+// false when a buffer was too small (the cloud is then recomputed singly).
+template <bool SB, bool SR>
+__device__ bool bit_reduce(Ctx c, const uint32_t* mat, uint64_t* back, int n, uint32_t thr, const uint32_t* ucur,
+                           int nu, uint32_t arena2_off, size_t arena2_bytes, PairRec* h1tmp, int* nh1,
+                           unsigned long long& adds) {
+    const BitEng E = bit_setup<SB, SR>(back, mat, n, thr, arena2_off);
+    BitHead& H = bit_hd();
+    const size_t used2 = SR ? (((size_t)n * (n - 1) + 15) & ~(size_t)15) : 0;  // the ranks (2 bytes per edge)
+    const size_t hsz = (size_t)c.hmask + 1;
+    if (used2 + hsz * 12 <= arena2_bytes) {
+        uint64_t* hk = reinterpret_cast<uint64_t*>(g_bsm + arena2_off + used2);
+        uint32_t* hv = reinterpret_cast<uint32_t*>(g_bsm + arena2_off + used2 + hsz * 8);
+        for (size_t i = threadIdx.x; i < hsz; i += HT) { hk[i] = c.hkeys[i]; hv[i] = c.hvals[i]; }
+        c.hkeys = hk;
+        c.hvals = hv;
+        __syncthreads();
+    }
+    adds = 0;
+    for (int q = 0; q < nu; ++q) {
+        const int j = (int)ucur[q];
+        const uint64_t self_key = c.cols[j];
+        unsigned long long col_adds;
+        int vl;
+        const uint64_t key = bit_column<SB, SR>(E, c, mat, j, col_adds, vl);
+        adds += col_adds;
+        if (H.fail) return false;
+        if (col_adds) {  // keep R_j as its generators: j, then those recorded
+            if (threadIdx.x == 0) H.poff = atomicAdd(c.pool_used, (unsigned long long)(vl + 1));
+            __syncthreads();
+            const unsigned long long off = H.poff;
+            if ((int64_t)(off + vl + 1) > c.pool_cap) return false;
+            for (int i = threadIdx.x; i <= vl; i += HT) c.pool[off + i] = i == 0 ? (self_key & c.cmask) : E.vbuf[i - 1];
+            if (threadIdx.x == 0) {
+                c.rc_ptr[j] = (uint64_t)(c.pool + off);
+                c.rc_len[j] = (uint32_t)(vl + 1);
+            }
+        }
+        if (threadIdx.x == 0) {
+            Simplex<1> s;
+            load_col<1>(c, self_key, s);
+            PairRec pr;
+            pr.birth_rank = s.r;
+            pr.birth_cidx = s.cidx;
+            bool out = true;
+            if (key == EMPTY) {
+                pr.death_rank = 0xFFFFFFFFu; pr.death_cidx = -1;
+            } else {
+                pr.death_rank = (uint32_t)(key >> TRI_BITS);
+                pr.death_cidx = (int64_t)(c.rcmask - (key & c.rcmask));
+                hash_insert(c, (uint64_t)pr.death_cidx, (uint32_t)j);
+                out = pr.death_rank > pr.birth_rank;
+            }
+            if (out) h1tmp[(*nh1)++] = pr;
+        }
+        if (q + 1 < nu) bit_clear<SB, SR>(E, (int)(self_key & c.cmask), vl);
+        __syncthreads();
+    }
+    return true;
 }
 
 __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
@@ -531,76 +1095,23 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
             nu = nn;
         }
         VR_PHASE(5);
-        // 5c. the remaining columns in order, each to completion (block engine)
+        // 5c. the remaining columns in order, each to completion (bitmap engine)
         if (A.prof && threadIdx.x == 0) atomicAdd(A.prof + 8, (unsigned long long)nu);
         unsigned long long adds = 0;
-        for (int q = 0; q < nu; ++q) {
-            const int j = ucur[q];
-            const uint64_t self_key = cols[j];
-            Simplex<1> s;
-            load_col<1>(c, self_key, s);
-            if (threadIdx.x == 0) { S.fsize = 0; S.bsize = 0; S.holes = 0; S.Ks = EMPTY; S.cur = 0; }
-            __syncthreads();
-            bool ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, s);
-            uint64_t key = EMPTY;
-            unsigned long long col_adds = 0;
-            uint64_t prev = 0;  // pivot before the last addition
-            int pre = 0;  // owner kind of the current pivot if probed during the last merge (3: none)
-            while (ok) {
-                if (++col_adds > (1ull << 22)) { ok = false; break; }  // far beyond any column: flag the cloud
-                if (S.fsize == 0 && !heavy_refill<8>(S, back)) { key = EMPTY; break; }
-                key = S.buf[S.cur][0];
-                // A column finished here keeps no reduced form, so its owner's
-                // coboundary D_o stands in for R_o: a valid column operation, but
-                // one that may leave the pivot in place and then repeat forever.
-                // An unchanged pivot sends the cloud to the single-cloud path.
-                if (col_adds > 1 && key == prev) { ok = false; break; }
-                prev = key;
-                const int kind = pre ? (pre == 3 ? 0 : pre) : heavy_owner_probe<1>(c, S, key, self_key);
-                pre = 0;
-                if (kind == 0) break;
-                if (kind == 1) {
-                    const int64_t opos = S.opos;
-                    if (c.rc_len[opos]) {
-                        ok = heavy_add_stored<1>(c, S, back, BACKCAP, opos);
-                    } else {
-                        Simplex<1> o;
-                        load_col<1>(c, cols[opos], o);
-                        ok = heavy_add_coboundary<1>(c, S, back, BACKCAP, o);
-                    }
-                } else {
-                    // the next pivot's owner is probed during the merge (one pass covers
-                    // n <= 256): 85.4 -> 80.8 ms on the 4096-cloud batch, 5.55 -> 5.22 ms
-                    // on the 256 circles, where one long cocycle column per cloud holds
-                    // nearly all the additions
-                    const int r = heavy_apparent_add<1, true>(c, S, back, BACKCAP, self_key, &pre);
-                    if (r < 0) break;  // the pivot has no owner: the column is complete
-                    ok = r > 0;
-                }
-                ++adds;
-                __syncthreads();
-            }
+        if (nu > 0) {
+            // the block engine's space is the arena; the per-point buffers (points,
+            // clearing bits, tree, H0 records), no longer needed, the second arena
+            constexpr uint32_t a2 = (uint32_t)offsetof(BatchSmem, pts);
+            constexpr size_t a2b = offsetof(BatchSmem, h0) + sizeof(PairRec) * BMAXN - offsetof(BatchSmem, pts);
+            const int var = bit_variant(n, sizeof(HeavySmem), a2b);
+            const bool ok = var == 0   ? bit_reduce<true, true>(c, mat, back, n, thr, ucur, nu, a2, a2b, h1tmp, &M.nh1, adds)
+                            : var == 1 ? bit_reduce<false, true>(c, mat, back, n, thr, ucur, nu, a2, a2b, h1tmp, &M.nh1, adds)
+                                       : bit_reduce<false, false>(c, mat, back, n, thr, ucur, nu, a2, a2b, h1tmp, &M.nh1,
+                                                                  adds);
             if (!ok) {
                 if (threadIdx.x == 0) M.overflow = 1;
                 __syncthreads();
-                break;
             }
-            if (threadIdx.x == 0) {
-                PairRec pr;
-                pr.birth_rank = s.r;
-                pr.birth_cidx = s.cidx;
-                bool out = true;
-                if (key == EMPTY) {
-                    pr.death_rank = 0xFFFFFFFFu; pr.death_cidx = -1;
-                } else {
-                    pr.death_rank = (uint32_t)(key >> TRI_BITS);
-                    pr.death_cidx = (int64_t)(c.rcmask - (key & c.rcmask));
-                    hash_insert(c, (uint64_t)pr.death_cidx, (uint32_t)j);
-                    out = pr.death_rank > pr.birth_rank;
-                }
-                if (out) h1tmp[M.nh1++] = pr;
-            }
-            __syncthreads();
         }
         if (threadIdx.x == 0 && adds) atomicAdd(A.stats + 3, adds);
         VR_PHASE(6);
