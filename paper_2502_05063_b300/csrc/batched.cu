@@ -288,7 +288,9 @@ __device__ __forceinline__ void bit_clear_bucket(const BitEng& E, int r) {
 // lie at its diameter) leave its bit alone (set, and cleared only by the
 // count) and count whether they were set or cleared, summed per warp.
 // (Combining the other buckets' bits per warp first, lanes grouped by
-// target word, measured slower: 765 -> 3.8 K cycles per addition.)
+// target word, measured slower: 765 -> 3.8 K cycles per addition.  So did
+// flipping without counting, leaving an emptied bucket to its next search:
+// 2.89 -> 3.30 ms on 256 circles, 62.0 -> 65.9 ms on 4096 clouds.)
 template <bool SB, bool SR>
 __device__ __forceinline__ void bit_flip(const BitEng& E, bool on, uint32_t t, uint32_t d, int rp) {
     int delta = 0;
@@ -345,7 +347,9 @@ __device__ void bit_add_list(const BitEng& E, const uint64_t* list, int len, int
 
 // The pivot of W: false if W is zero, else the triangle {a, b, w} (a > b an
 // edge of bucket r) with the largest index among the rows of the lowest
-// non-empty bucket r.  rp, cp: the previous pivot's bucket (-1: none) and
+// non-empty bucket r, and whether the edges (a, w) and (b, w) also have rank
+// r (eq_aw, eq_bw): a search result packs (index << 10) | (w << 2) |
+// (eq_aw << 1) | eq_bw.  rp, cp: the previous pivot's bucket (-1: none) and
 // the rows its search found; with the rows the last addition set or
 // cleared there (H.dcnt) they tell whether it emptied, in which case its
 // bit is cleared first.  Every warp finds the lowest set bucket bit itself
@@ -355,7 +359,7 @@ __device__ void bit_add_list(const BitEng& E, const uint64_t* list, int len, int
 // zeroed after search i's barrier, when search i - 1's slot has been read.
 template <bool SB, bool SR>
 __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, uint32_t& a_out, uint32_t& b_out,
-                          uint32_t& w_out, uint32_t& t_out, int& c_out) {
+                          uint32_t& w_out, uint32_t& t_out, int& c_out, bool& eq_aw, bool& eq_bw) {
     BitHead& H = bit_hd();
     const uint16_t* G = bit_G<SB>(E);
     const uint16_t* Es = bit_Es(E);
@@ -395,7 +399,7 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
             const uint32_t word = bit_word<SB>(E, t >> 5), ra = rk[bit_eidx(a, w)], rb = rk[bit_eidx(b, w)];
             if (!((word >> (t & 31)) & 1u) || ra > (uint32_t)r || rb > (uint32_t)r) continue;  // absent, or another bucket's
             ++found;
-            atomicMax(&H.best[sl], (t << 8) | (uint32_t)w);
+            atomicMax(&H.best[sl], (t << 10) | ((uint32_t)w << 2) | ((ra == (uint32_t)r) << 1) | (rb == (uint32_t)r));
         }
         if (found) atomicAdd(&H.cnt[sl], found);
         __syncthreads();
@@ -404,13 +408,15 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
         if (threadIdx.x == 0) { H.best[(it + 2) % 3] = 0; H.cnt[(it + 2) % 3] = 0; }
         ++it;
         if (cnt) {
-            const uint32_t t = best >> 8, w = best & 0xFFu;
+            const uint32_t t = best >> 10, w = (best >> 2) & 0xFFu;
             uint32_t a = ab0 >> 8, b = ab0 & 0xFFu;
             for (int ei = 1; ei < k && !(a != w && b != w && bit_tidx(a, b, w) == t); ++ei) {  // ties only
                 a = Es[g0 + ei] >> 8;
                 b = Es[g0 + ei] & 0xFFu;
             }
             r_out = r; t_out = t; w_out = w; a_out = a; b_out = b; c_out = cnt;
+            eq_aw = (best >> 1) & 1u;
+            eq_bw = best & 1u;
             if (threadIdx.x == 0) H.dcnt = 0;  // counted from the caller's next barrier on
             return true;
         }
@@ -583,7 +589,8 @@ __device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* ma
     for (;;) {
         int r, cf;
         uint32_t a, b, w, t;
-        if (!bit_pivot<SB, SR>(E, rp, cp, it, r, a, b, w, t, cf)) break;
+        bool eq_aw, eq_bw;
+        if (!bit_pivot<SB, SR>(E, rp, cp, it, r, a, b, w, t, cf, eq_aw, eq_bw)) break;
         rp = r;
         cp = cf;
         // warp 15 (no vertex of its own) probes the hash of finished columns;
@@ -594,10 +601,9 @@ __device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* ma
             const int64_t hp = warp_hash_find(c, t);
             if (threadIdx.x == HT - 32) H.opos = (int)hp;
         }
-        const uint32_t ra = rk[bit_eidx(a, w)], rb = rk[bit_eidx(b, w)];
         uint32_t wd = w;
-        if (rb == (uint32_t)r && a > wd) wd = a;
-        if (ra == (uint32_t)r && b > wd) wd = b;
+        if (eq_bw && a > wd) wd = a;  // the edge opposite a is (b, w)
+        if (eq_aw && b > wd) wd = b;
         const uint32_t su = wd == a ? b : a, sv = wd == w ? b : w;  // s' = {a, b, w} - {wd}
         bool row = false, older = false;
         uint32_t rt = 0, d = 0;
