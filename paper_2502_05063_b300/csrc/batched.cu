@@ -217,12 +217,15 @@ constexpr int64_t BIT_G = BIT_RK + 8192;                                       /
 constexpr int64_t BIT_ES = BIT_G + 8200;                                       // u16 edges by distance
 constexpr int64_t BIT_BITS = BIT_ES + 8192;                                    // u32 bitmap, C(256,3) bits
 constexpr int64_t BIT_V = BIT_BITS + ((int64_t)BMAXN * (BMAXN - 1) * (BMAXN - 2) / 6 + 63) / 64;
-static_assert(BIT_V + BIT_VCAP <= BACKCAP, "the bitmap engine's scratch fits the back buffer");
+constexpr int64_t BIT_KEYS2 = BIT_V + BIT_VCAP;  // partitioned sort keys, 32768, then room to sort a crowded range
+static_assert(BIT_KEYS2 + 65536 <= BACKCAP, "the bitmap engine's scratch fits the back buffer");
+constexpr int BIT_CHUNK = 8192;  // keys sorted at once in shared memory
 static_assert(BMAXN * (BMAXN - 1) / 2 < 0xFFFF, "dense ranks fit 16 bits below the above-threshold mark");
 
 struct BitHead {
     uint32_t best[3];         // pivot search results, (index << 8) | w, the largest wins; used in rotation
     int cnt[3];               // rows found by the same searches (a tie may count a row twice)
+    uint32_t lo, hi;          // setup: the smallest and largest distance bits within the threshold
     int dcnt;                 // rows of the last pivot's bucket the last addition set (+1) or cleared (-1)
     int opos;                 // position of the finished column owning the pivot, or -1
     int fail;
@@ -424,6 +427,72 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
     }
 }
 
+// Sort keys[0..m) ((distance bits << 16) | edge, distance bits in [lo, hi])
+// in global memory, using the arena from byte hb: BIT_CHUNK keys, then the
+// partition's tables.  The keys are partitioned into 256 ranges of distance
+// bits (a histogram, a scan and a scatter into tmp), consecutive ranges are
+// grouped into chunks of at most BIT_CHUNK keys, and each chunk is sorted by
+// a bitonic network in shared memory and written back; the ranges being
+// ordered, the chunks follow one another.  A range above BIT_CHUNK keys
+// (distances crowded into a narrow band) is sorted in global memory, in
+// tmp[32768..).
+__device__ void bit_sort_keys(uint64_t* keys, uint64_t* tmp, int m, uint32_t lo, uint32_t hi, uint32_t hb) {
+    uint64_t* sk = reinterpret_cast<uint64_t*>(g_bsm + hb);
+    int* rstart = reinterpret_cast<int*>(g_bsm + hb + BIT_CHUNK * 8);  // [257]
+    int* rcur = rstart + 257;                                          // [256]
+    int* cbeg = rcur + 256;                                            // [257], then the chunk count
+    const uint64_t span = (uint64_t)hi - lo + 1;
+    auto range_of = [&](uint64_t k) { return (int)((((k >> 16) - lo) * 256) / span); };
+    for (int i = threadIdx.x; i < 256; i += HT) rcur[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += HT) atomicAdd(&rcur[range_of(keys[i])], 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 counts by one warp, 8 per lane
+        int v[8], sum = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) { v[u] = rcur[threadIdx.x * 8 + u]; sum += v[u]; }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)threadIdx.x >= o) incl += y;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) { rstart[threadIdx.x * 8 + u] = run; rcur[threadIdx.x * 8 + u] = run; run += v[u]; }
+        if (threadIdx.x == 31) rstart[256] = run;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += HT) {
+        const uint64_t k = keys[i];
+        tmp[atomicAdd(&rcur[range_of(k)], 1)] = k;
+    }
+    if (threadIdx.x == 0) {  // chunks: maximal runs of ranges within BIT_CHUNK keys
+        int c = 0, b = 0;
+        cbeg[0] = 0;
+        while (b < 256) {
+            int e = b + 1;
+            while (e < 256 && rstart[e + 1] - rstart[b] <= BIT_CHUNK) ++e;
+            cbeg[++c] = rstart[e];
+            b = e;
+        }
+        cbeg[257] = c;
+    }
+    __syncthreads();
+    const int nch = cbeg[257];
+    for (int ch = 0; ch < nch; ++ch) {
+        const int c0 = cbeg[ch], len = cbeg[ch + 1] - c0;
+        int l2 = 1;
+        while (l2 < len) l2 <<= 1;
+        uint64_t* buf = len > BIT_CHUNK ? tmp + 32768 : sk;  // a crowded range: global room of 32768
+        for (int i = threadIdx.x; i < l2; i += HT) buf[i] = i < len ? tmp[c0 + i] : EMPTY;
+        __syncthreads();
+        block_bitonic(buf, l2);
+        for (int i = threadIdx.x; i < len; i += HT) keys[c0 + i] = buf[i];
+        __syncthreads();
+    }
+}
+
 // Which variant a cloud of n points takes, for the worst case (every edge
 // within the threshold, all distances distinct): 0 = SB and SR (head,
 // bucket bits, bucket starts, edges by distance and bitmap in the arena, the
@@ -465,9 +534,10 @@ __device__ BitEng bit_setup(uint64_t* back, const uint32_t* mat, int n, uint32_t
     E.grk = reinterpret_cast<const uint16_t*>(back + BIT_RK);
     // 1. the edges within the threshold, as (distance bits << 16) | edge, in
     // any order (they are sorted next); four distances in flight per thread
-    if (threadIdx.x == 0) H.cnt[0] = 0;  // the append counter (search slots are zeroed per column)
+    if (threadIdx.x == 0) { H.cnt[0] = 0; H.lo = 0xFFFFFFFFu; H.hi = 0; }  // append counter (search slots are zeroed per column)
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    uint32_t lo = 0xFFFFFFFFu, hi = 0;
     for (int base = 0; base < ne; base += 4 * HT) {
         uint32_t d[4];
         int e[4];
@@ -489,16 +559,27 @@ __device__ BitEng bit_setup(uint64_t* back, const uint32_t* mat, int n, uint32_t
             int at = 0;
             if (lane == 0 && bl) at = atomicAdd(&H.cnt[0], __popc(bl));
             at = __shfl_sync(0xffffffffu, at, 0);
-            if (keep) keys[at + __popc(bl & ((1u << lane) - 1u))] = ((uint64_t)d[u] << 16) | (uint64_t)e[u];
+            if (keep) {
+                keys[at + __popc(bl & ((1u << lane) - 1u))] = ((uint64_t)d[u] << 16) | (uint64_t)e[u];
+                lo = min(lo, d[u]);
+                hi = max(hi, d[u]);
+            }
         }
     }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) { atomicMin(&H.lo, lo); atomicMax(&H.hi, hi); }
     __syncthreads();
     const int m = H.cnt[0];
     int len = 1;
     while (len < m) len <<= 1;
-    for (int i = m + (int)threadIdx.x; i < len; i += HT) keys[i] = EMPTY;
-    __syncthreads();
-    block_bitonic(keys, len);
+    if constexpr (SB) {  // all keys fit the arena
+        for (int i = m + (int)threadIdx.x; i < len; i += HT) keys[i] = EMPTY;
+        __syncthreads();
+        block_bitonic(keys, len);
+    } else {
+        bit_sort_keys(keys, back + BIT_KEYS2, m, H.lo, H.hi, hb);
+    }
     // 2. buckets: runs of equal distance
     int nR = 0;
     for (int base = 0; base < m; base += HT) {
