@@ -207,6 +207,9 @@ typedef struct {
     int32_t* critical_edges[2];         /* 4 per pair if VR_CRITICAL_EDGES, else NULL;
                                            rows of the packed `pts` array (not cloud-local) */
     float* thresholds;                  /* float[num_clouds]: threshold used per cloud  */
+    int32_t recomputed;                 /* clouds that outgrew a per-block buffer of the
+                                           persistent launch and were computed by the
+                                           single-cloud path instead (same results)     */
 } vr_batch_result;
 
 vr_status vr_barcodes_batched(const float* pts, const int64_t* offsets, int32_t num_clouds,
@@ -226,6 +229,7 @@ typedef struct {
     int32_t* critical_edges[2];         /* device, 4 per pair if VR_CRITICAL_EDGES, else NULL */
     float* thresholds;                  /* host, float[num_clouds]                          */
     void* stream;                       /* the call's stream (used by the free)             */
+    int32_t recomputed;                 /* as in vr_batch_result                            */
 } vr_batch_device_result;
 
 vr_status vr_barcodes_batched_device(const float* pts, const int64_t* offsets, int32_t num_clouds,

@@ -1602,6 +1602,7 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
         int codes[8] = {0};
         for (int i = 0; i < num_clouds; ++i)
             if (cerr[i]) { bad.push_back(i); codes[cerr[i] & 7]++; }
+        res->recomputed = (int32_t)bad.size();
         if (log_enabled() && !bad.empty())
             fprintf(stderr, "[vr] batch: %zu clouds recomputed singly (codes 1:%d 2:%d 3:%d 4:%d)\n", bad.size(),
                     codes[1], codes[2], codes[3], codes[4]);
@@ -1756,6 +1757,7 @@ extern "C" vr_status vr_barcodes_batched_device(const float* pts, const int64_t*
     }
     d->thresholds = r->thresholds;
     r->thresholds = nullptr;
+    d->recomputed = r->recomputed;
     vr_batch_result_free(r);
     *out = d;
     return VR_OK;

@@ -71,7 +71,7 @@ class BatchResult(ctypes.Structure):
                 ("pair_offsets", ctypes.POINTER(ctypes.c_int64) * 2),
                 ("pairs", ctypes.POINTER(Pair) * 2),
                 ("critical_edges", ctypes.POINTER(ctypes.c_int32) * 2),
-                ("thresholds", ctypes.POINTER(ctypes.c_float))]
+                ("thresholds", ctypes.POINTER(ctypes.c_float)), ("recomputed", ctypes.c_int32)]
 
 
 class DeviceResult(ctypes.Structure):
@@ -87,7 +87,8 @@ class BatchDeviceResult(ctypes.Structure):
                 ("pair_offsets", ctypes.POINTER(ctypes.c_int64) * 2),
                 ("pairs", ctypes.c_void_p * 2),
                 ("critical_edges", ctypes.c_void_p * 2),
-                ("thresholds", ctypes.POINTER(ctypes.c_float)), ("stream", ctypes.c_void_p)]
+                ("thresholds", ctypes.POINTER(ctypes.c_float)), ("stream", ctypes.c_void_p),
+                ("recomputed", ctypes.c_int32)]
 
 
 PAIR_DTYPE = np.dtype([("birth", "<f4"), ("death", "<f4"), ("birth_simplex", "<u8"), ("death_simplex", "<i8")])
@@ -211,6 +212,7 @@ class BatchBarcodes:
 
     def __init__(self, res: BatchResult):
         self.num_clouds, self.dmax = res.num_clouds, res.dmax
+        self.recomputed = res.recomputed  # clouds computed by the single-cloud path instead
         self.pairs, self.offsets, self.critical_edges = [], [], []
         nc = res.num_clouds
         self.thresholds = np.ctypeslib.as_array(res.thresholds, shape=(max(nc, 1),))[:nc].copy()
@@ -371,6 +373,7 @@ class DeviceBatchBarcodes:
         import torch
         nc = res.num_clouds
         self.num_clouds, self.dmax = nc, res.dmax
+        self.recomputed = res.recomputed
         self.thresholds = np.ctypeslib.as_array(res.thresholds, shape=(max(nc, 1),))[:nc].copy()
         self.values, self.edges, self.offsets = [], [], []
         for p in range(res.dmax + 1):

@@ -47,6 +47,7 @@ def test_batched_equals_single(vr, dmax, thr, flags):
     clouds = mixed_clouds(60, seed=dmax * 10 + int(np.isfinite(thr)))
     pts, offs = synth.pack(clouds)
     bb = vr.barcodes_batched(pts, offs, dmax=dmax, threshold=thr, flags=flags)
+    assert bb.recomputed == 0
     for i, c in enumerate(clouds):
         single = vr.barcodes(points=c, dmax=dmax, threshold=thr, flags=flags)
         for p in range(dmax + 1):
@@ -67,6 +68,7 @@ def test_batch4096_workload(vr):
     clouds, kinds = synth.batch_clouds()
     pts, offs = synth.pack(clouds)
     bb = vr.barcodes_batched(torch.from_numpy(pts).cuda(), offs, dmax=1)
+    assert bb.recomputed == 0  # every cloud came from the persistent launch itself
     sample = list(range(0, len(clouds), 8))
     dgs = pool.diagrams([clouds[i] for i in sample], 1)
     for i, dg in zip(sample, dgs):
@@ -95,6 +97,37 @@ def test_batched_repeat_and_shapes(vr):
     with pytest.raises(vr.VRError):
         big = np.zeros((300, 3), np.float32)
         vr.barcodes_batched(big, np.array([0, 300]), dmax=1)
+
+
+@pytest.mark.parametrize("n", [100, 150, 256])
+def test_lattice_ties(vr, n):
+    """Points of a 3x3x3 grid: few distinct distances, so most diameter
+    buckets hold many edges and the edge keys crowd a few distance ranges;
+    one size per storage variant of the dimension-1 engine (everything in
+    shared memory up to 128 points, the ranks up to 172, neither above)."""
+    rng = np.random.default_rng(n)
+    clouds = [rng.integers(0, 3, size=(n, 3)).astype(np.float32) for _ in range(3)]
+    pts, offs = synth.pack(clouds)
+    bb = vr.barcodes_batched(pts, offs, dmax=1)
+    assert bb.recomputed == 0
+    for i, c in enumerate(clouds):
+        single = vr.barcodes(points=c, dmax=1)
+        for p in range(2):
+            assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
+
+
+def test_circles_need_no_recompute(vr):
+    """The 256 noisy circles of the differentiable workload: the persistent
+    launch computes every cloud itself (none is handed to the single-cloud
+    path), and each equals the single-cloud path."""
+    circ = synth.circles()
+    pts, offs = synth.pack(circ)
+    bb = vr.barcodes_batched(pts, offs, dmax=1)
+    assert bb.recomputed == 0
+    for i in range(0, len(circ), 5):
+        single = vr.barcodes(points=circ[i], dmax=1)
+        for p in range(2):
+            assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
 
 
 def test_batched_output_larger_than_planned(vr):
