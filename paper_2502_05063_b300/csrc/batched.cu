@@ -220,6 +220,8 @@ constexpr int64_t BIT_V = BIT_BITS + ((int64_t)BMAXN * (BMAXN - 1) * (BMAXN - 2)
 constexpr int64_t BIT_KEYS2 = BIT_V + BIT_VCAP;  // partitioned sort keys, 32768, then room to sort a crowded range
 static_assert(BIT_KEYS2 + 65536 <= BACKCAP, "the bitmap engine's scratch fits the back buffer");
 constexpr int BIT_CHUNK = 8192;  // keys sorted at once in shared memory
+constexpr int BAT_DSM_N = 197;   // largest n whose distances (upper triangle) fit the arena in steps 1-3
+constexpr int BAT_LOCK = 8;      // lock-step candidate vertices of the apparent search
 static_assert(BMAXN * (BMAXN - 1) / 2 < 0xFFFF, "dense ranks fit 16 bits below the above-threshold mark");
 
 struct BitHead {
@@ -867,7 +869,12 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
             tp = t_;                                                         \
         }                                                                    \
     } while (0)
-        // ---- 1. points and distances (bits of the single-precision formula)
+        // ---- 1. points and distances (bits of the single-precision formula);
+        // up to BAT_DSM_N points the upper triangle is also kept in the arena
+        // (the engine's space, unused until 5c) for the spanning tree and the
+        // apparent search
+        const bool dsh = n <= BAT_DSM_N;
+        uint32_t* dsm = reinterpret_cast<uint32_t*>(g_bsm);
         for (int i = threadIdx.x; i < n * A.dim; i += HT) M.pts[i] = A.pts[o0 * A.dim + i];
         for (int i = threadIdx.x; i < (ne + 31) / 32; i += HT) M.clear[i] = 0;
         __syncthreads();
@@ -884,16 +891,23 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
                 bits = __float_as_uint(__fsqrt_rn(acc));
             }
             mat[i * BLD + j] = bits;
+            if (dsh && i > j) dsm[i * (i - 1) / 2 + j] = bits;
         }
         __syncthreads();
         const RankMatrix R{mat, n, BLD};
+        // distances for steps 2-3: the arena's copy when it holds one (shared
+        // memory), else the matrix in global memory
+        auto D = [&](int i, int j) -> uint32_t {
+            if (dsh) return i == j ? 0u : dsm[i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i];
+            return R(i, j);
+        };
         // ---- 2. threshold: enclosing radius unless given
         if (threadIdx.x == 0) M.thr = A.thr_inf ? 0xFFFFFFFFu : A.thr_bits;
         __syncthreads();
         if (A.thr_inf) {
             for (int i = wid; i < n; i += HW) {
                 uint32_t m = 0;
-                for (int j = lane; j < n; j += 32) m = max(m, R(i, j));
+                for (int j = lane; j < n; j += 32) m = max(m, D(i, j));
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
                 if (lane == 0) atomicMin(&M.thr, m);
@@ -934,7 +948,7 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
                 for (int q = 0; q < BMAXN / 32; ++q) {
                     const int v = lane + 32 * q;
                     if (v < n && !((intree >> q) & 1u)) {
-                        const uint32_t r = R(u, v);
+                        const uint32_t r = D(u, v);
                         if (r <= thr) {
                             const int a = u > v ? u : v, b = u > v ? v : u;
                             const uint64_t key = ((uint64_t)r << 32) | (0xFFFFFFFFull - (uint64_t)(a * (a - 1) / 2 + b));
@@ -978,7 +992,12 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
                 M.h0n = h;
             }
         } else if (A.dmax >= 1) {
-            // ---- 3b. warps 1..15: apparent pairs of the edges within the threshold
+            // ---- 3b. warps 1..15: apparent pairs of the edges within the threshold.
+            // Each lane takes an edge s = (a, b) of the chunk and tests, in lock
+            // step with the other lanes, the candidate vertices w = n-1, n-2, ...
+            // (the oldest cofacet of s is s + {w} for the largest w keeping the
+            // diameter) for BAT_LOCK steps; the edges still open then search the
+            // rest one at a time, 32 candidates per warp step.
             unsigned long long c_app = 0, c_cand = 0;
             for (int ch = wid - 1; ch * 32 < ne; ch += HW - 1) {
                 const int e = ch * 32 + lane;
@@ -987,43 +1006,57 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
                 bool kept = false;
                 if (e < ne) {
                     edge_of(e, va, vb);
-                    r = R(va, vb);
+                    r = D(va, vb);
                     kept = r <= thr;
                     c_cand += kept;
                 }
-                uint32_t km = __ballot_sync(0xffffffffu, kept);
-                while (km) {
-                    const int src = __ffs(km) - 1;
-                    km &= km - 1;
-                    const int a = __shfl_sync(0xffffffffu, va, src), b = __shfl_sync(0xffffffffu, vb, src);
-                    const uint32_t sr = __shfl_sync(0xffffffffu, r, src);
-                    const int se = __shfl_sync(0xffffffffu, e, src);
-                    int wf = -1;
-                    for (int base = n - 1; base >= 0; base -= 32) {
-                        const int w = base - lane;
-                        const bool ok = w >= 0 && w != a && w != b && R(a, w) <= sr && R(b, w) <= sr;
-                        const uint32_t bl = __ballot_sync(0xffffffffu, ok);
-                        if (bl) { wf = base - (__ffs(bl) - 1); break; }
-                    }
-                    // facet t - {x} for a vertex x > wf of s must not keep the diameter
-                    bool apparent = wf >= 0;
-                    if (apparent && a > wf && R(b, wf) == sr) apparent = false;
-                    if (apparent && b > wf && R(a, wf) == sr) apparent = false;
-                    if (lane == 0) {
-                        if (apparent) ++c_app;
-                        else {
-                            const int at = atomicAdd(&M.ncols, 1);
-                            if (at < CCAP) cols[at] = ((~(uint64_t)sr & 0xFFFFFFFFull) << EDGE_BITS) | (uint64_t)se;
-                            else M.overflow = 1;
-                        }
+                int wf = -1;
+                bool open = kept;
+#pragma unroll
+                for (int k = 0; k < BAT_LOCK; ++k) {
+                    const int w = n - 1 - k;
+                    if (open && w >= 0 && w != va && w != vb && D(va, w) <= r && D(vb, w) <= r) {
+                        wf = w;
+                        open = false;
                     }
                 }
-            }
-            if (lane == 0) {
-                if (c_app) atomicAdd(A.stats + 1, c_app);
+                if (n - 1 - BAT_LOCK < 0) open = false;  // every candidate tested
+                uint32_t om = __ballot_sync(0xffffffffu, open);
+                while (om) {
+                    const int src = __ffs(om) - 1;
+                    om &= om - 1;
+                    const int a = __shfl_sync(0xffffffffu, va, src), b = __shfl_sync(0xffffffffu, vb, src);
+                    const uint32_t sr = __shfl_sync(0xffffffffu, r, src);
+                    int f = -1;
+                    for (int base = n - 1 - BAT_LOCK; base >= 0; base -= 32) {
+                        const int w = base - lane;
+                        const bool ok = w >= 0 && w != a && w != b && D(a, w) <= sr && D(b, w) <= sr;
+                        const uint32_t bl = __ballot_sync(0xffffffffu, ok);
+                        if (bl) { f = base - (__ffs(bl) - 1); break; }
+                    }
+                    if (lane == src) wf = f;
+                }
+                // facet t - {x} for a vertex x > wf of s must not keep the diameter
+                bool apparent = kept && wf >= 0;
+                if (apparent && va > wf && D(vb, wf) == r) apparent = false;
+                if (apparent && vb > wf && D(va, wf) == r) apparent = false;
+                c_app += apparent;
+                const bool col = kept && !apparent;
+                const uint32_t cm = __ballot_sync(0xffffffffu, col);
+                int at = 0;
+                if (lane == 0 && cm) at = atomicAdd(&M.ncols, __popc(cm));
+                at = __shfl_sync(0xffffffffu, at, 0) + __popc(cm & ((1u << lane) - 1u));
+                if (col) {
+                    if (at < CCAP) cols[at] = ((~(uint64_t)r & 0xFFFFFFFFull) << EDGE_BITS) | (uint64_t)e;
+                    else M.overflow = 1;
+                }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c_cand += __shfl_xor_sync(0xffffffffu, c_cand, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                c_cand += __shfl_xor_sync(0xffffffffu, c_cand, o);
+                c_app += __shfl_xor_sync(0xffffffffu, c_app, o);
+            }
+            if (lane == 0 && c_app) atomicAdd(A.stats + 1, c_app);
             if (lane == 0 && c_cand) atomicAdd(A.stats + 0, c_cand);
         }
         __syncthreads();
