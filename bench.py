@@ -32,6 +32,7 @@ and the value is the work of all ranks over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -426,21 +427,29 @@ def batched_metrics(stream, steps=20):
     from paper_2502_05063_b300 import autograd, synth, vr
 
     def timeit(fn, k):
-        """Median ms of k timed calls (CUDA events per call) after 3 warm-up calls, and the spread."""
+        """Median ms of k timed calls (CUDA events per call) after 3 warm-up calls, and the spread.
+        Python's cyclic garbage collector is paused during the timed calls (as the
+        standard timeit module does), so an interpreter-wide collection over the
+        bench process's objects does not land in one call's time."""
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
         ms = []
-        for _ in range(k):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
+        gc.collect()
+        gc.disable()
+        try:
+            for _ in range(k):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        finally:
+            gc.enable()
         ms.sort()
         spread = {"min": ms[0], "p10": ms[len(ms) // 10], "median": statistics.median(ms),
-                  "p90": ms[(9 * len(ms)) // 10], "max": ms[-1], "repeats": k}
+                  "p90": ms[(9 * len(ms)) // 10], "max": ms[-1], "repeats": k, "python_gc": "paused while timed"}
         return statistics.median(ms), spread
 
     clouds, _ = synth.batch_clouds()
@@ -709,16 +718,17 @@ def run_single():
     return 0
 
 
-def run_single_batched(num):
-    """One batched call on the first `num` clouds of the 4096-cloud workload (for
-    profiler captures of the persistent kernel)."""
+def run_single_batched(num, circles=False):
+    """One batched call on the first `num` clouds of the 4096-cloud workload, or
+    on the 256 circles of the differentiable workload (for profiler captures of
+    the persistent kernel)."""
     import torch
     from paper_2502_05063_b300 import synth, vr
-    clouds, _ = synth.batch_clouds()
-    pts, offs = synth.pack(clouds[:num])
+    clouds = synth.circles() if circles else synth.batch_clouds()[0][:num]
+    pts, offs = synth.pack(clouds)
     bb = vr.barcodes_batched(torch.from_numpy(pts).cuda(), offs, dmax=1)
     torch.cuda.synchronize()
-    print(json.dumps({"clouds": num, "pairs": [int(o[-1]) for o in bb.offsets]}))
+    print(json.dumps({"clouds": len(clouds), "pairs": [int(o[-1]) for o in bb.offsets]}))
     return 0
 
 
@@ -734,11 +744,15 @@ def main():
                     help="one untimed call of the workload (for profiler captures), prints its stage counts")
     ap.add_argument("--single-batched", type=int, default=0, metavar="N",
                     help="one batched call on the first N clouds of the 4096-cloud workload (profiler captures)")
+    ap.add_argument("--single-circles", action="store_true",
+                    help="one batched call on the 256 circles of the differentiable workload (profiler captures)")
     args = ap.parse_args()
     if args.single:
         return run_single()
     if args.single_batched:
         return run_single_batched(args.single_batched)
+    if args.single_circles:
+        return run_single_batched(0, circles=True)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

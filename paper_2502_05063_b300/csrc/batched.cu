@@ -1448,8 +1448,13 @@ BatchPlan* make_plan(int dev, int num, int dim, int dmax, int want_edges, int th
 }
 
 // Launch shape: persistent blocks per SM (1 or 2), picked by timing both on
-// the first batch of a given mean cloud size and remembered per device.
+// the first batch of more clouds than SMs of a given mean cloud size and
+// remembered per device.
 int tuned_slots(BatchPlan& P, cudaStream_t s, int sms, int64_t bucket) {
+    // no more clouds than SMs: one block per SM runs every cloud at once, each
+    // alone on its SM; nothing is timed or remembered (a batch this small would
+    // time both shapes alike and fix the choice for larger batches)
+    if (P.num <= sms) return 1;
     const auto key = std::make_pair(P.device, bucket);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) return it->second;

@@ -171,7 +171,7 @@ class Barcodes:
             m = res.count[p]
             if m:
                 buf = ctypes.cast(res.pairs[p], ctypes.POINTER(ctypes.c_char * (m * PAIR_DTYPE.itemsize))).contents
-                self.pairs.append(np.frombuffer(bytes(buf), dtype=PAIR_DTYPE).copy())
+                self.pairs.append(np.frombuffer(buf, dtype=PAIR_DTYPE).copy())
             else:
                 self.pairs.append(np.zeros(0, dtype=PAIR_DTYPE))
             if res.critical_edges[p]:
@@ -221,7 +221,7 @@ class BatchBarcodes:
             m = int(off[-1])
             if m:
                 buf = ctypes.cast(res.pairs[p], ctypes.POINTER(ctypes.c_char * (m * PAIR_DTYPE.itemsize))).contents
-                arr = np.frombuffer(bytes(buf), dtype=PAIR_DTYPE).copy()
+                arr = np.frombuffer(buf, dtype=PAIR_DTYPE).copy()
             else:
                 arr = np.zeros(0, dtype=PAIR_DTYPE)
             edges = None
