@@ -225,8 +225,9 @@ constexpr int BAT_LOCK = 8;      // lock-step candidate vertices of the apparent
 static_assert(BMAXN * (BMAXN - 1) / 2 < 0xFFFF, "dense ranks fit 16 bits below the above-threshold mark");
 
 struct BitHead {
-    uint32_t best[3];         // pivot search results, (index << 8) | w, the largest wins; used in rotation
+    uint32_t best[3];         // pivot search results (packed, see bit_pivot), the largest wins; used in rotation
     int cnt[3];               // rows found by the same searches (a tie may count a row twice)
+    int rr[3];                // the buckets they searched (-1: W is zero)
     uint32_t lo, hi;          // setup: the smallest and largest distance bits within the threshold
     int dcnt;                 // rows of the last pivot's bucket the last addition set (+1) or cleared (-1)
     int opos;                 // position of the finished column owning the pivot, or -1
@@ -357,8 +358,10 @@ __device__ void bit_add_list(const BitEng& E, const uint64_t* list, int len, int
 // (eq_aw << 1) | eq_bw.  rp, cp: the previous pivot's bucket (-1: none) and
 // the rows its search found; with the rows the last addition set or
 // cleared there (H.dcnt) they tell whether it emptied, in which case its
-// bit is cleared first.  Every warp finds the lowest set bucket bit itself
-// (a warp minimum over the words, no barrier); a bucket whose search finds
+// bit is cleared first.  Each warp covering the third vertices finds the
+// lowest set bucket bit itself (a warp minimum over the words, no barrier)
+// and searches its share; the bucket and the result reach every thread
+// through the result slots after one barrier.  A bucket whose search finds
 // nothing is cleared and the next one searched.  `it` counts the searches
 // of the column: the result slot of search i is i mod 3, and slot i + 2 is
 // zeroed after search i's barrier, when search i - 1's slot has been read.
@@ -370,51 +373,62 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
     const uint16_t* Es = bit_Es(E);
     const uint16_t* rk = bit_rk<SR>(E);
     const uint32_t* h0 = bit_h0(E);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (E.nR + 31) >> 5;
-    if (rp >= 0 && cp + H.dcnt <= 0) bit_clear_bucket(E, rp);
+    // the warps covering the n third vertices search; the others wait at the
+    // barrier and take the bucket from the result slot
+    const int sw = (E.n + 31) >> 5;
+    const bool searcher = wid < sw;
+    if (searcher && rp >= 0 && cp + H.dcnt <= 0) bit_clear_bucket(E, rp);
     for (;;) {
-        // the lowest non-empty word: eight words per lane loaded at once, lane
-        // i taking words i, i + 32, ...; a batch with a set bit ends the search
-        uint32_t lw = 0xFFFFFFFFu;
-        for (int base = 0; base < nw; base += 256) {
-            uint32_t v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = base + u * 32 + lane;
-                v[u] = i < nw ? h0[i] : 0u;
-            }
-#pragma unroll
-            for (int u = 7; u >= 0; --u)
-                if (v[u]) lw = (uint32_t)(base + u * 32 + lane);
-            if (__any_sync(0xffffffffu, lw != 0xFFFFFFFFu)) break;
-        }
-        lw = __reduce_min_sync(0xffffffffu, lw);
-        if (lw == 0xFFFFFFFFu) return false;
-        const int r = (int)(lw * 32 + __ffs(h0[lw]) - 1);
-        const int g0 = E.ident ? r : (int)G[r], k = E.ident ? 1 : (int)G[r + 1] - g0;
-        const uint32_t ab0 = Es[g0];  // the bucket's first (usually only) edge
         const int sl = it % 3;
-        int found = 0;
-        for (int idx = threadIdx.x; idx < k * E.n; idx += HT) {
-            const int ei = k == 1 ? 0 : idx / E.n, w = idx - ei * E.n;
-            const uint32_t ab = ei == 0 ? ab0 : Es[g0 + ei], a = ab >> 8, b = ab & 0xFFu;
-            if (w == (int)a || w == (int)b) continue;
-            const uint32_t t = bit_tidx(a, b, w);
-            const uint32_t word = bit_word<SB>(E, t >> 5), ra = rk[bit_eidx(a, w)], rb = rk[bit_eidx(b, w)];
-            if (!((word >> (t & 31)) & 1u) || ra > (uint32_t)r || rb > (uint32_t)r) continue;  // absent, or another bucket's
-            ++found;
-            atomicMax(&H.best[sl], (t << 10) | ((uint32_t)w << 2) | ((ra == (uint32_t)r) << 1) | (rb == (uint32_t)r));
+        if (searcher) {
+            // the lowest non-empty word: eight words per lane loaded at once,
+            // lane i taking words i, i + 32, ...; a batch with a set bit ends it
+            uint32_t lw = 0xFFFFFFFFu;
+            for (int base = 0; base < nw; base += 256) {
+                uint32_t v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = base + u * 32 + lane;
+                    v[u] = i < nw ? h0[i] : 0u;
+                }
+#pragma unroll
+                for (int u = 7; u >= 0; --u)
+                    if (v[u]) lw = (uint32_t)(base + u * 32 + lane);
+                if (__any_sync(0xffffffffu, lw != 0xFFFFFFFFu)) break;
+            }
+            lw = __reduce_min_sync(0xffffffffu, lw);
+            const int r = lw == 0xFFFFFFFFu ? -1 : (int)(lw * 32 + __ffs(h0[lw]) - 1);
+            if (threadIdx.x == 0) H.rr[sl] = r;
+            if (r >= 0) {
+                const int g0 = E.ident ? r : (int)G[r], k = E.ident ? 1 : (int)G[r + 1] - g0;
+                const uint32_t ab0 = Es[g0];  // the bucket's first (usually only) edge
+                int found = 0;
+                for (int idx = threadIdx.x; idx < k * E.n; idx += sw * 32) {
+                    const int ei = k == 1 ? 0 : idx / E.n, w = idx - ei * E.n;
+                    const uint32_t ab = ei == 0 ? ab0 : Es[g0 + ei], a = ab >> 8, b = ab & 0xFFu;
+                    if (w == (int)a || w == (int)b) continue;
+                    const uint32_t t = bit_tidx(a, b, w);
+                    const uint32_t word = bit_word<SB>(E, t >> 5), ra = rk[bit_eidx(a, w)], rb = rk[bit_eidx(b, w)];
+                    if (!((word >> (t & 31)) & 1u) || ra > (uint32_t)r || rb > (uint32_t)r) continue;  // absent, or another bucket's
+                    ++found;
+                    atomicMax(&H.best[sl], (t << 10) | ((uint32_t)w << 2) | ((ra == (uint32_t)r) << 1) | (rb == (uint32_t)r));
+                }
+                if (found) atomicAdd(&H.cnt[sl], found);
+            }
         }
-        if (found) atomicAdd(&H.cnt[sl], found);
         __syncthreads();
+        const int r = H.rr[sl];
         const uint32_t best = H.best[sl];
         const int cnt = H.cnt[sl];
         if (threadIdx.x == 0) { H.best[(it + 2) % 3] = 0; H.cnt[(it + 2) % 3] = 0; }
         ++it;
+        if (r < 0) return false;
         if (cnt) {
+            const int g0 = E.ident ? r : (int)G[r], k = E.ident ? 1 : (int)G[r + 1] - g0;
             const uint32_t t = best >> 10, w = (best >> 2) & 0xFFu;
-            uint32_t a = ab0 >> 8, b = ab0 & 0xFFu;
+            uint32_t a = Es[g0] >> 8, b = Es[g0] & 0xFFu;
             for (int ei = 1; ei < k && !(a != w && b != w && bit_tidx(a, b, w) == t); ++ei) {  // ties only
                 a = Es[g0 + ei] >> 8;
                 b = Es[g0 + ei] & 0xFFu;
@@ -425,7 +439,7 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
             if (threadIdx.x == 0) H.dcnt = 0;  // counted from the caller's next barrier on
             return true;
         }
-        bit_clear_bucket(E, r);  // bucket r is empty
+        if (searcher) bit_clear_bucket(E, r);  // bucket r is empty
     }
 }
 
@@ -1341,7 +1355,7 @@ struct BatchPlan {
 
 std::mutex g_batch_mutex;
 BatchPlan* g_plan = nullptr;
-std::map<std::pair<int, int64_t>, int> g_tuned;  // (device, mean-size bucket) -> slots per SM
+std::map<std::pair<int, int64_t>, int> g_tuned;  // (device, size bucket) -> slots per SM
 
 size_t slot_bytes() {
     return (size_t)BMAXN * BLD * 4 + (size_t)HCAP * 12 +
@@ -1448,8 +1462,8 @@ BatchPlan* make_plan(int dev, int num, int dim, int dmax, int want_edges, int th
 }
 
 // Launch shape: persistent blocks per SM (1 or 2), picked by timing both on
-// the first batch of more clouds than SMs of a given mean cloud size and
-// remembered per device.
+// the first batch of more clouds than SMs of a given size bucket (mean cloud
+// size and number of clouds) and remembered per device.
 int tuned_slots(BatchPlan& P, cudaStream_t s, int sms, int64_t bucket) {
     // no more clouds than SMs: one block per SM runs every cloud at once, each
     // alone on its SM; nothing is timed or remembered (a batch this small would
@@ -1572,7 +1586,11 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
                                 dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         VR_CUDA(cudaMemcpyAsync(P->offs, offsets, (num_clouds + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         VR_CUDA(cudaMemcpyAsync(P->order, order.data(), num_clouds * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        const int64_t bucket = total / num_clouds / 32;
+        // tuned per (mean cloud size / 32, number of clouds rounded up to a power of
+        // two): the better shape depends on both
+        int lg = 0;
+        while ((1 << lg) < num_clouds) ++lg;
+        const int64_t bucket = (total / num_clouds / 32) * 64 + lg;
         const int per = tuned_slots(*P, s, sms, bucket);
         if (P->slots != per * sms || !P->exec || P->captured_on != s) {
             P->slots = per * sms;
