@@ -58,6 +58,7 @@ struct BatchArgs {
     uint32_t thr_bits;     // used when !thr_inf
     int thr_inf;
     int want_edges;
+    int64_t pool_cap;      // stored generators per cloud (POOLCAP; smaller under VR_BATCH_POOL_CAP, for tests)
     // per-slot scratch
     uint32_t* mat;
     uint64_t* hkeys;
@@ -1137,7 +1138,7 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
         c.err = A.cloud_err + cloud;
         c.pool = A.pool + slot * POOLCAP;
         c.pool_used = A.pool_used + slot;
-        c.pool_cap = POOLCAP;
+        c.pool_cap = A.pool_cap;
         c.rc_ptr = A.rc_off + slot * (int64_t)CCAP;
         c.mode = MODE_EXPLICIT;
         c.rc_len = A.rc_len + slot * (int64_t)CCAP;
@@ -1424,6 +1425,11 @@ BatchPlan* make_plan(int dev, int num, int dim, int dmax, int want_edges, int th
         A.back = carve<uint64_t>(cur, (size_t)slots * BACKCAP);
         A.wstage = carve<uint64_t>(cur, (size_t)slots * HW * STAGE);
         A.pool = carve<uint64_t>(cur, (size_t)slots * POOLCAP);
+        A.pool_cap = POOLCAP;
+        if (const char* pc = getenv("VR_BATCH_POOL_CAP")) {  // test-only: force the single-cloud recompute
+            const long long v = atoll(pc);
+            A.pool_cap = v < 1 ? 1 : (v > POOLCAP ? POOLCAP : v);
+        }
         A.pool_used = carve<unsigned long long>(cur, (size_t)slots);
         A.rc_off = carve<uint64_t>(cur, (size_t)slots * CCAP);
         A.rc_len = carve<uint32_t>(cur, (size_t)slots * CCAP);

@@ -116,6 +116,22 @@ def test_lattice_ties(vr, n):
             assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
 
 
+def test_recompute_when_generators_overflow(vr, monkeypatch):
+    """With the per-cloud store of generators cut to 8 entries (read when a
+    plan is built; this shape is used by no other test, so the plan is new),
+    the long cocycle column of each circle outgrows it: those clouds are
+    handed to the single-cloud path, and every cloud still equals it."""
+    monkeypatch.setenv("VR_BATCH_POOL_CAP", "8")
+    circ = synth.circles(num=24, n=100, seed=9)
+    pts, offs = synth.pack(circ)
+    bb = vr.barcodes_batched(pts, offs, dmax=1)
+    assert bb.recomputed > 0
+    for i, c in enumerate(circ):
+        single = vr.barcodes(points=c, dmax=1)
+        for p in range(2):
+            assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
+
+
 def test_circles_need_no_recompute(vr):
     """The 256 noisy circles of the differentiable workload: the persistent
     launch computes every cloud itself (none is handed to the single-cloud
