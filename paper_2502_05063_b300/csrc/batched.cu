@@ -245,8 +245,26 @@ struct BitEng {
     const uint16_t* grk;  // dense rank per edge index, 0xFFFF above the threshold
     uint64_t* vbuf;       // generators of the current column (edge indices)
     int n, nbw, nR;
+    int nt;               // threads of the column loop: the warps covering the n vertices, then one for the hash
     bool ident;           // every bucket holds one edge (no two distances tie): bucket r is Es[r]
 };
+
+// The column loop runs on the first E.nt threads (the warps covering the
+// cloud's vertices and one more, which probes the hash), synchronized by
+// named barrier 1; the block's other warps wait for the whole reduction at
+// a block barrier instead of taking part in every step.
+__device__ __forceinline__ void bit_sync(const BitEng& E) {
+    asm volatile("bar.sync 1, %0;" ::"r"(E.nt) : "memory");
+}
+__device__ __forceinline__ int bit_sync_or(const BitEng& E, int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred), "r"(E.nt)
+        : "memory");
+    return r;
+}
 
 __device__ __forceinline__ BitHead& bit_hd() { return *reinterpret_cast<BitHead*>(g_bsm); }
 __device__ __forceinline__ uint32_t* bit_h0(const BitEng& E) { return reinterpret_cast<uint32_t*>(g_bsm + E.o_h0); }
@@ -334,21 +352,15 @@ __device__ __forceinline__ void bit_cob(const BitEng& E, int u, int v, uint32_t 
 }
 
 // W <- W + sum of D_g over the generators g (edge indices) in list[0..len),
-// two generators per pass (n <= 256 vertices each).
+// one generator per pass of the loop's threads (more than n of them).
 template <bool SB, bool SR>
 __device__ void bit_add_list(const BitEng& E, const uint64_t* list, int len, int rp) {
-    for (int base = 0; base < len; base += HT / BMAXN) {
-        const int gi = base + (int)(threadIdx.x / BMAXN);
-        const int w = (int)(threadIdx.x % BMAXN);
-        int u = 0, v = 0;
-        uint32_t rs = 0;
-        const bool ok = gi < len && w < E.n;
-        if (ok) {
-            const int e = (int)list[gi];
-            edge_of(e, u, v);
-            rs = bit_rk<SR>(E)[e];
-        }
-        bit_cob<SB, SR>(E, u, v, rs, ok ? w : -1, rp);
+    const int w = (int)threadIdx.x < E.n ? (int)threadIdx.x : -1;
+    for (int gi = 0; gi < len; ++gi) {
+        const int e = (int)list[gi];
+        int u, v;
+        edge_of(e, u, v);
+        bit_cob<SB, SR>(E, u, v, bit_rk<SR>(E)[e], w, rp);
     }
 }
 
@@ -419,7 +431,7 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
                 if (found) atomicAdd(&H.cnt[sl], found);
             }
         }
-        __syncthreads();
+        bit_sync(E);
         const int r = H.rr[sl];
         const uint32_t best = H.best[sl];
         const int cnt = H.cnt[sl];
@@ -623,6 +635,7 @@ __device__ BitEng bit_setup(uint64_t* back, const uint32_t* mat, int n, uint32_t
     if (threadIdx.x == 0) Gg[nR] = (uint16_t)m;
     E.nR = nR;
     E.ident = nR == m;
+    E.nt = 32 * ((n + 31) / 32 + 1);
     const int64_t ntri = (int64_t)n * (n - 1) * (n - 2) / 6;
     E.nbw = (int)((ntri + 31) / 32);
     __syncthreads();
@@ -679,7 +692,7 @@ __device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* ma
     const int x = (int)threadIdx.x;  // this thread's third vertex
     bit_cob<SB, SR>(E, ja, jb, rj, x < E.n ? x : -1, -1);
     if (threadIdx.x < 3) { H.best[threadIdx.x] = 0; H.cnt[threadIdx.x] = 0; }
-    __syncthreads();
+    bit_sync(E);
     uint64_t key = EMPTY;
     adds = 0;
     vl = 0;
@@ -691,13 +704,13 @@ __device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* ma
         if (!bit_pivot<SB, SR>(E, rp, cp, it, r, a, b, w, t, cf, eq_aw, eq_bw)) break;
         rp = r;
         cp = cf;
-        // warp 15 (no vertex of its own) probes the hash of finished columns;
+        // the loop's last warp (no vertex of its own) probes the hash of finished columns;
         // meanwhile every thread finds the candidate apparent owner s' (the
         // facet left by dropping the largest vertex whose opposite edge keeps
         // the diameter; w's is (a, b)) and tests its own cofacet of s'
-        if (threadIdx.x >= HT - 32) {
+        if ((int)threadIdx.x >= E.nt - 32) {  // the last warp of the loop, with no vertex of its own
             const int64_t hp = warp_hash_find(c, t);
-            if (threadIdx.x == HT - 32) H.opos = (int)hp;
+            if ((int)threadIdx.x == E.nt - 32) H.opos = (int)hp;
         }
         uint32_t wd = w;
         if (eq_bw && a > wd) wd = a;  // the edge opposite a is (b, w)
@@ -712,7 +725,7 @@ __device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* ma
             row = d != 0xFFFFu;
             rt = bit_tidx(su, sv, x);
         }
-        const int any_older = __syncthreads_or(older);
+        const int any_older = bit_sync_or(E, older);
         const int opos = H.opos;
         if (opos < 0 && any_older) {  // the pivot has no owner: the column is complete
             key = ((uint64_t)mat[a * BLD + b] << TRI_BITS) | (c.rcmask - t);
@@ -735,7 +748,7 @@ __device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* ma
             }
             if (len) {
                 bit_add_list<SB, SR>(E, lst, (int)len, r);
-                for (int i = threadIdx.x; i < (int)len; i += HT) E.vbuf[vl + i] = lst[i];
+                for (int i = threadIdx.x; i < (int)len; i += E.nt) E.vbuf[vl + i] = lst[i];
             } else {
                 int oa, ob;
                 edge_of((int)eo, oa, ob);
@@ -757,9 +770,9 @@ __device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* ma
             if (threadIdx.x == 0) E.vbuf[vl] = es;
             vl += 1;
         }
-        __syncthreads();
+        bit_sync(E);
     }
-    __syncthreads();  // H.fail is read by every thread after the return
+    bit_sync(E);  // H.fail is read by every thread of the loop after the return
     return key;
 }
 
@@ -767,7 +780,7 @@ __device__ uint64_t bit_column(const BitEng& E, const Ctx& c, const uint32_t* ma
 // flipped back, a longer record is cheaper to wipe; the bucket bits are reset.
 template <bool SB, bool SR>
 __device__ void bit_clear(const BitEng& E, int ej, int vl) {
-    __syncthreads();
+    bit_sync(E);
     if (!SB && vl < 8) {
         int ja, jb;
         edge_of(ej, ja, jb);
@@ -776,12 +789,12 @@ __device__ void bit_clear(const BitEng& E, int ej, int vl) {
         bit_add_list<SB, SR>(E, E.vbuf, vl, -1);
     } else {
         uint4* bw = reinterpret_cast<uint4*>(bit_bits<SB>(E));
-        for (int i = threadIdx.x; i < (E.nbw + 3) / 4; i += HT) bw[i] = make_uint4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < (E.nbw + 3) / 4; i += E.nt) bw[i] = make_uint4(0, 0, 0, 0);
     }
-    __syncthreads();
+    bit_sync(E);
     uint32_t* h0 = bit_h0(E);
-    for (int i = threadIdx.x; i < (E.nR + 31) / 32; i += HT) h0[i] = 0;
-    __syncthreads();
+    for (int i = threadIdx.x; i < (E.nR + 31) / 32; i += E.nt) h0[i] = 0;
+    bit_sync(E);
 }
 
 // 5c for one cloud: the columns ucur[0..nu) in order, each reduced to
@@ -805,46 +818,53 @@ __device__ bool bit_reduce(Ctx c, const uint32_t* mat, uint64_t* back, int n, ui
         __syncthreads();
     }
     adds = 0;
-    for (int q = 0; q < nu; ++q) {
-        const int j = (int)ucur[q];
-        const uint64_t self_key = c.cols[j];
-        unsigned long long col_adds;
-        int vl;
-        const uint64_t key = bit_column<SB, SR>(E, c, mat, j, col_adds, vl);
-        adds += col_adds;
-        if (H.fail) return false;
-        if (col_adds) {  // keep R_j as its generators: j, then those recorded
-            if (threadIdx.x == 0) H.poff = atomicAdd(c.pool_used, (unsigned long long)(vl + 1));
-            __syncthreads();
-            const unsigned long long off = H.poff;
-            if ((int64_t)(off + vl + 1) > c.pool_cap) return false;
-            for (int i = threadIdx.x; i <= vl; i += HT) c.pool[off + i] = i == 0 ? (self_key & c.cmask) : E.vbuf[i - 1];
+    if ((int)threadIdx.x < E.nt) {  // the column loop (the other warps wait at the barrier below)
+        for (int q = 0; q < nu; ++q) {
+            const int j = (int)ucur[q];
+            const uint64_t self_key = c.cols[j];
+            unsigned long long col_adds;
+            int vl;
+            const uint64_t key = bit_column<SB, SR>(E, c, mat, j, col_adds, vl);
+            adds += col_adds;
+            if (H.fail) break;
+            if (col_adds) {  // keep R_j as its generators: j, then those recorded
+                if (threadIdx.x == 0) H.poff = atomicAdd(c.pool_used, (unsigned long long)(vl + 1));
+                bit_sync(E);
+                const unsigned long long off = H.poff;
+                if ((int64_t)(off + vl + 1) > c.pool_cap) {
+                    if (threadIdx.x == 0) H.fail = 1;
+                    break;
+                }
+                for (int i = threadIdx.x; i <= vl; i += E.nt)
+                    c.pool[off + i] = i == 0 ? (self_key & c.cmask) : E.vbuf[i - 1];
+                if (threadIdx.x == 0) {
+                    c.rc_ptr[j] = (uint64_t)(c.pool + off);
+                    c.rc_len[j] = (uint32_t)(vl + 1);
+                }
+            }
             if (threadIdx.x == 0) {
-                c.rc_ptr[j] = (uint64_t)(c.pool + off);
-                c.rc_len[j] = (uint32_t)(vl + 1);
+                Simplex<1> s;
+                load_col<1>(c, self_key, s);
+                PairRec pr;
+                pr.birth_rank = s.r;
+                pr.birth_cidx = s.cidx;
+                bool out = true;
+                if (key == EMPTY) {
+                    pr.death_rank = 0xFFFFFFFFu; pr.death_cidx = -1;
+                } else {
+                    pr.death_rank = (uint32_t)(key >> TRI_BITS);
+                    pr.death_cidx = (int64_t)(c.rcmask - (key & c.rcmask));
+                    hash_insert(c, (uint64_t)pr.death_cidx, (uint32_t)j);
+                    out = pr.death_rank > pr.birth_rank;
+                }
+                if (out) h1tmp[(*nh1)++] = pr;
             }
+            if (q + 1 < nu) bit_clear<SB, SR>(E, (int)(self_key & c.cmask), vl);
+            bit_sync(E);
         }
-        if (threadIdx.x == 0) {
-            Simplex<1> s;
-            load_col<1>(c, self_key, s);
-            PairRec pr;
-            pr.birth_rank = s.r;
-            pr.birth_cidx = s.cidx;
-            bool out = true;
-            if (key == EMPTY) {
-                pr.death_rank = 0xFFFFFFFFu; pr.death_cidx = -1;
-            } else {
-                pr.death_rank = (uint32_t)(key >> TRI_BITS);
-                pr.death_cidx = (int64_t)(c.rcmask - (key & c.rcmask));
-                hash_insert(c, (uint64_t)pr.death_cidx, (uint32_t)j);
-                out = pr.death_rank > pr.birth_rank;
-            }
-            if (out) h1tmp[(*nh1)++] = pr;
-        }
-        if (q + 1 < nu) bit_clear<SB, SR>(E, (int)(self_key & c.cmask), vl);
-        __syncthreads();
     }
-    return true;
+    __syncthreads();
+    return !H.fail;
 }
 
 __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
