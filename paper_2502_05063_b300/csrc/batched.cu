@@ -1372,7 +1372,42 @@ struct BatchPlan {
     int32_t* edges[2] = {nullptr, nullptr};
     cudaGraphExec_t exec = nullptr;
     cudaStream_t captured_on = nullptr;
+    // pinned staging of host results (device-to-host copies into pageable
+    // memory run at a fraction of the link's rate), grown on demand
+    char* pin = nullptr;
+    size_t pin_bytes = 0;
 };
+
+// Copy `bytes` from device memory into pageable host memory through the
+// plan's pinned staging buffer (chunks of at most 8 MB, the copy of one
+// chunk overlapping the host copy of the previous one).
+void copy_to_host(BatchPlan& P, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return;
+    constexpr size_t CH = (size_t)8 << 20;
+    if (!P.pin) {
+        VR_CUDA(cudaMallocHost((void**)&P.pin, 2 * CH));
+        P.pin_bytes = 2 * CH;
+    }
+    cudaEvent_t done[2];
+    VR_CUDA(cudaEventCreateWithFlags(&done[0], cudaEventDisableTiming));
+    VR_CUDA(cudaEventCreateWithFlags(&done[1], cudaEventDisableTiming));
+    const size_t nch = (bytes + CH - 1) / CH;
+    for (size_t k = 0; k <= nch; ++k) {
+        if (k < nch) {  // queue chunk k into half k % 2
+            const size_t len = std::min(CH, bytes - k * CH);
+            VR_CUDA(cudaMemcpyAsync(P.pin + (k & 1) * CH, static_cast<const char*>(src) + k * CH, len,
+                                    cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaEventRecord(done[k & 1], s));
+        }
+        if (k > 0) {  // chunk k - 1 is on the host once its event completes
+            const size_t j = k - 1, len = std::min(CH, bytes - j * CH);
+            VR_CUDA(cudaEventSynchronize(done[j & 1]));
+            memcpy(static_cast<char*>(dst) + j * CH, P.pin + (j & 1) * CH, len);
+        }
+    }
+    cudaEventDestroy(done[0]);
+    cudaEventDestroy(done[1]);
+}
 
 std::mutex g_batch_mutex;
 BatchPlan* g_plan = nullptr;
@@ -1387,6 +1422,7 @@ size_t slot_bytes() {
 void free_plan(BatchPlan* p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->pin) cudaFreeHost(p->pin);
     cudaFree(p->pts); cudaFree(p->offs); cudaFree(p->order); cudaFree(p->scratch); cudaFree(p->outbuf);
     delete p;
 }
@@ -1726,12 +1762,9 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
                 res->critical_edges[p] = (int32_t*)malloc(std::max<int64_t>(off[num_clouds], 1) * 4 * sizeof(int32_t));
             if (!res->pairs[p] || (want_edges && !res->critical_edges[p])) throw Error{VR_ERR_OOM};
             if (bad.empty()) {
-                VR_CUDA(cudaMemcpyAsync(res->pairs[p], P->pairs[p], off[num_clouds] * sizeof(vr_pair),
-                                        cudaMemcpyDeviceToHost, s));
+                copy_to_host(*P, res->pairs[p], P->pairs[p], off[num_clouds] * sizeof(vr_pair), s);
                 if (want_edges)
-                    VR_CUDA(cudaMemcpyAsync(res->critical_edges[p], P->edges[p], off[num_clouds] * 4 * sizeof(int32_t),
-                                            cudaMemcpyDeviceToHost, s));
-                VR_CUDA(cudaStreamSynchronize(s));
+                    copy_to_host(*P, res->critical_edges[p], P->edges[p], off[num_clouds] * 4 * sizeof(int32_t), s);
             } else {
                 std::vector<vr_pair> dv(std::max<int64_t>(res->pair_offsets[p][num_clouds], 1));
                 std::vector<int32_t> de(want_edges ? 4 * dv.size() : 0);

@@ -206,11 +206,34 @@ def barcodes(points=None, dists=None, n=None, dmax=1, threshold=np.inf, flags=0,
         lib.vr_result_free(out)
 
 
+class _ResultHolder:
+    """Frees a library result once the last array viewing its memory is gone."""
+
+    def __init__(self, ptr, free):
+        self.ptr, self.free = ptr, free
+
+    def __del__(self):
+        try:
+            self.free(self.ptr)
+        except Exception:  # interpreter shutdown: the library may already be unloaded
+            pass
+
+
+def _view(ptr, nbytes, dtype, holder):
+    """numpy view of nbytes of library-owned host memory, keeping `holder` (and so
+    the memory) alive as long as the view or any array derived from it."""
+    buf = ctypes.cast(ptr, ctypes.POINTER(ctypes.c_char * nbytes)).contents
+    buf.holder = holder
+    return np.frombuffer(buf, dtype=dtype)
+
+
 class BatchBarcodes:
     """Pairs of many clouds: pairs[p] (structured array of all clouds, cloud i at
-    offsets[p][i]:offsets[p][i+1]), critical_edges[p] or None, thresholds[i]."""
+    offsets[p][i]:offsets[p][i+1]), critical_edges[p] or None, thresholds[i].
+    The pair and edge arrays view the library's result in place (no copy); it
+    is released when the last of them is gone."""
 
-    def __init__(self, res: BatchResult):
+    def __init__(self, res: BatchResult, holder=None):
         self.num_clouds, self.dmax = res.num_clouds, res.dmax
         self.recomputed = res.recomputed  # clouds computed by the single-cloud path instead
         self.pairs, self.offsets, self.critical_edges = [], [], []
@@ -219,14 +242,19 @@ class BatchBarcodes:
         for p in range(res.dmax + 1):
             off = np.ctypeslib.as_array(res.pair_offsets[p], shape=(nc + 1,)).copy()
             m = int(off[-1])
-            if m:
+            if m and holder is not None:
+                arr = _view(res.pairs[p], m * PAIR_DTYPE.itemsize, PAIR_DTYPE, holder)
+            elif m:
                 buf = ctypes.cast(res.pairs[p], ctypes.POINTER(ctypes.c_char * (m * PAIR_DTYPE.itemsize))).contents
                 arr = np.frombuffer(buf, dtype=PAIR_DTYPE).copy()
             else:
                 arr = np.zeros(0, dtype=PAIR_DTYPE)
             edges = None
             if res.critical_edges[p]:
-                edges = np.ctypeslib.as_array(res.critical_edges[p], shape=(max(m, 1) * 4,))[: 4 * m].reshape(m, 4).copy()
+                if m and holder is not None:
+                    edges = _view(res.critical_edges[p], m * 16, np.int32, holder).reshape(m, 4)
+                else:
+                    edges = np.ctypeslib.as_array(res.critical_edges[p], shape=(max(m, 1) * 4,))[: 4 * m].reshape(m, 4).copy()
             self.pairs.append(arr)
             self.offsets.append(off)
             self.critical_edges.append(edges)
@@ -244,10 +272,8 @@ def barcodes_batched(points, offsets, dmax=1, threshold=np.inf, flags=0, stream=
     code = lib.vr_barcodes_batched(ptr, offs.ctypes.data, len(offs) - 1, int(points.shape[1]), int(dmax),
                                    float(threshold), int(flags), _stream_ptr(stream), ctypes.byref(out))
     _check(code, "vr_barcodes_batched")
-    try:
-        return BatchBarcodes(out.contents)
-    finally:
-        lib.vr_batch_result_free(out)
+    holder = _ResultHolder(out, lib.vr_batch_result_free)  # frees `out` when its last view goes
+    return BatchBarcodes(out.contents, holder)
 
 
 def simplex_vertices(cidx: int, q: int, n: int):
