@@ -92,3 +92,34 @@ def test_product_path_has_no_oracle_dependency():
     for f in os.listdir(os.path.join(ROOT, "paper_2502_05063_b300", "csrc")):
         text = open(os.path.join(ROOT, "paper_2502_05063_b300", "csrc", f)).read()
         assert "vr_oracle" not in text and "or_cohom" not in text
+
+
+def test_binding_structs_match_the_header(vr, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets of
+    its C struct in include/vr.h (a C program built here prints them), so a
+    field added to the header without the binding, or in another order, fails."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"vr_pair": vr.Pair, "vr_stats": vr.Stats, "vr_result": vr.Result,
+               "vr_batch_result": vr.BatchResult, "vr_device_result": vr.DeviceResult,
+               "vr_batch_device_result": vr.BatchDeviceResult, "vr_hypha_stats": vr.HyphaStats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "vr.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
