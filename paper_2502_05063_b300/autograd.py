@@ -19,30 +19,31 @@ import torch
 from . import vr
 
 
-def _edges_tensor(bc, dmax, device):
-    """Critical edges of every dimension, concatenated (device tensors from the
-    device-resident result: no host round trip)."""
-    parts = [bc.edges[p] for p in range(dmax + 1)]
-    return torch.cat(parts).to(device) if parts else torch.zeros((0, 4), dtype=torch.int32, device=device)
+def _edges_of(bc, p, device):
+    """Critical edges of dimension p (a device tensor of the device-resident
+    result: no host round trip)."""
+    e = bc.edges[p]
+    return e.to(device) if e is not None else torch.zeros((0, 4), dtype=torch.int32, device=device)
 
 
 class VRDiagram(torch.autograd.Function):
     """VRDiagram.apply(points (n, D) float32 CUDA, dmax, threshold=inf, recompute=False)
     -> tuple of (k_p, 2) tensors of (birth, death), p = 0..dmax; death = inf for
-    essential classes."""
+    essential classes.  Backward launches the library's kernel once per dimension
+    whose values received a gradient."""
 
     @staticmethod
     def forward(ctx, points, dmax, threshold=float("inf"), recompute=False):
+        ctx.set_materialize_grads(False)
         x = points.detach().contiguous()
         stream = torch.cuda.current_stream(x.device)
         bc = vr.barcodes_device(points=x, dmax=dmax, threshold=threshold, flags=vr.VR_CRITICAL_EDGES, stream=stream)
         outs = [bc.values[p] for p in range(dmax + 1)]
         ctx.dmax, ctx.threshold, ctx.recompute = dmax, threshold, recompute
-        ctx.counts = list(bc.counts)
         if recompute:
             ctx.save_for_backward(points)
         else:
-            ctx.save_for_backward(points, _edges_tensor(bc, dmax, x.device))
+            ctx.save_for_backward(points, *[_edges_of(bc, p, x.device) for p in range(dmax + 1)])
         return tuple(outs)
 
     @staticmethod
@@ -52,23 +53,18 @@ class VRDiagram(torch.autograd.Function):
             x = points.detach().contiguous()
             bc = vr.barcodes_device(points=x, dmax=ctx.dmax, threshold=ctx.threshold, flags=vr.VR_CRITICAL_EDGES,
                                     stream=torch.cuda.current_stream(x.device))
-            edges = _edges_tensor(bc, ctx.dmax, x.device)
+            edges = [_edges_of(bc, p, x.device) for p in range(ctx.dmax + 1)]
         else:
-            points, edges = ctx.saved_tensors
+            points, *edges = ctx.saved_tensors
             x = points.detach().contiguous()
-        gb, gd = [], []
-        for p, k in enumerate(ctx.counts):
-            g = grads[p]
-            if g is None:
-                g = torch.zeros((k, 2), dtype=torch.float32, device=x.device)
-            g = g.contiguous().float()
-            gb.append(g[:, 0])
-            gd.append(g[:, 1])
-        gb = torch.cat(gb).contiguous()
-        gd = torch.cat(gd).contiguous()
         grad = torch.zeros_like(x)
-        if edges.shape[0]:
-            vr.backward(x, edges.contiguous(), gb, gd, grad, stream=torch.cuda.current_stream(x.device))
+        stream = torch.cuda.current_stream(x.device)
+        for p in range(ctx.dmax + 1):
+            g = grads[p]
+            if g is None or edges[p].shape[0] == 0:
+                continue
+            g = g.float()
+            vr.backward(x, edges[p].contiguous(), g[:, 0].contiguous(), g[:, 1].contiguous(), grad, stream=stream)
         return grad, None, None, None
 
 
@@ -76,10 +72,12 @@ class VRDiagramBatched(torch.autograd.Function):
     """VRDiagramBatched.apply(points (sum n, D) float32 CUDA, offsets int64 host array,
     dmax, threshold=inf) -> for p = 0..dmax a (K_p, 2) tensor of all clouds' pairs,
     then for p = 0..dmax the int64 (num+1,) offsets of each cloud's pairs (no gradient).
-    One persistent launch forward, one backward launch for the whole batch."""
+    One persistent launch forward; backward, one launch per dimension whose values
+    received a gradient (dimensions without one cost nothing)."""
 
     @staticmethod
     def forward(ctx, points, offsets, dmax, threshold=float("inf")):
+        ctx.set_materialize_grads(False)
         x = points.detach().contiguous()
         offs = np.ascontiguousarray(offsets, dtype=np.int64)
         stream = torch.cuda.current_stream(x.device)
@@ -87,26 +85,22 @@ class VRDiagramBatched(torch.autograd.Function):
                                         stream=stream)
         outs = [bb.values[p] for p in range(dmax + 1)]
         offs_out = [torch.from_numpy(bb.offsets[p].astype(np.int64)) for p in range(dmax + 1)]
-        ctx.counts = [int(bb.offsets[p][-1]) for p in range(dmax + 1)]
-        ctx.save_for_backward(points, torch.cat([bb.edges[p] for p in range(dmax + 1)]))
+        ctx.dmax = dmax
+        ctx.save_for_backward(points, *[bb.edges[p] for p in range(dmax + 1)])
         for o in offs_out:
             ctx.mark_non_differentiable(o)
         return tuple(outs) + tuple(offs_out)
 
     @staticmethod
     def backward(ctx, *grads):
-        points, edges = ctx.saved_tensors
+        points, *edges = ctx.saved_tensors
         x = points.detach().contiguous()
-        gb, gd = [], []
-        for p, k in enumerate(ctx.counts):
-            g = grads[p]
-            if g is None:
-                g = torch.zeros((k, 2), dtype=torch.float32, device=x.device)
-            g = g.contiguous().float()
-            gb.append(g[:, 0])
-            gd.append(g[:, 1])
         grad = torch.zeros_like(x)
-        if edges.shape[0]:
-            vr.backward(x, edges.contiguous(), torch.cat(gb).contiguous(), torch.cat(gd).contiguous(), grad,
-                        stream=torch.cuda.current_stream(x.device))
+        stream = torch.cuda.current_stream(x.device)
+        for p in range(ctx.dmax + 1):
+            g = grads[p]
+            if g is None or edges[p].shape[0] == 0:
+                continue
+            g = g.float()
+            vr.backward(x, edges[p].contiguous(), g[:, 0].contiguous(), g[:, 1].contiguous(), grad, stream=stream)
         return grad, None, None, None
