@@ -220,7 +220,10 @@ void vr_batch_result_free(vr_batch_result* r);
 /* Device-resident variant of vr_barcodes_batched: the same pairs in the same
  * order; pairs[p] and critical_edges[p] are device pointers (allocated and,
  * by vr_batch_device_result_free, released in the order of `stream`, as for
- * vr_device_result), pair_offsets and thresholds host arrays. */
+ * vr_device_result), pair_offsets and thresholds host arrays.  The device
+ * arrays are written in the order of `stream` and the call returns without
+ * waiting for those copies: read them on `stream`, or after an event or
+ * synchronization on it. */
 typedef struct {
     int32_t num_clouds;
     int32_t dmax;

@@ -1669,12 +1669,21 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
             P->captured_on = s;
         }
         VR_CUDA(cudaGraphLaunch(P->exec, s));
-        // host reads: usage, per-cloud errors
+        // host reads, one wait: usage, per-cloud errors, thresholds, pair offsets
         unsigned long long used[2] = {0, 0};
-        VR_CUDA(cudaMemcpyAsync(used, P->args.used, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         std::vector<int32_t> cerr(num_clouds);
-        VR_CUDA(cudaMemcpyAsync(cerr.data(), P->args.cloud_err, num_clouds * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        VR_CUDA(cudaStreamSynchronize(s));
+        auto read_back = [&]() {
+            VR_CUDA(cudaMemcpyAsync(used, P->args.used, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaMemcpyAsync(cerr.data(), P->args.cloud_err, num_clouds * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaMemcpyAsync(res->thresholds, P->args.thr_used, num_clouds * sizeof(float),
+                                    cudaMemcpyDeviceToHost, s));
+            for (int p = 0; p <= dmax; ++p)
+                VR_CUDA(cudaMemcpyAsync(res->pair_offsets[p], P->off[p], (num_clouds + 1) * sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, s));
+            VR_CUDA(cudaStreamSynchronize(s));
+        };
+        read_back();
         if ((int64_t)used[0] > P->cap[0] || (int64_t)used[1] > P->cap[1]) {
             // output larger than planned: rebuild with room and rerun once
             int64_t ncap[2] = {std::max<int64_t>(P->cap[0], used[0]), std::max<int64_t>(P->cap[1], used[1] + 1024)};
@@ -1686,9 +1695,7 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
             VR_CUDA(cudaMemcpyAsync(P->offs, offsets, (num_clouds + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
             VR_CUDA(cudaMemcpyAsync(P->order, order.data(), num_clouds * sizeof(int32_t), cudaMemcpyHostToDevice, s));
             record_launches(*P, s);
-            VR_CUDA(cudaMemcpyAsync(cerr.data(), P->args.cloud_err, num_clouds * sizeof(int32_t),
-                                    cudaMemcpyDeviceToHost, s));
-            VR_CUDA(cudaStreamSynchronize(s));
+            read_back();
         }
         if (P->args.prof) {
             unsigned long long pr[16], st[4];
@@ -1711,11 +1718,6 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
             VR_CUDA(cudaMemset(P->args.prof, 0, 16 * sizeof(unsigned long long)));
         }
         // results in cloud order
-        VR_CUDA(cudaMemcpyAsync(res->thresholds, P->args.thr_used, num_clouds * sizeof(float), cudaMemcpyDeviceToHost, s));
-        for (int p = 0; p <= dmax; ++p)
-            VR_CUDA(cudaMemcpyAsync(res->pair_offsets[p], P->off[p], (num_clouds + 1) * sizeof(int64_t),
-                                    cudaMemcpyDeviceToHost, s));
-        VR_CUDA(cudaStreamSynchronize(s));
         std::vector<int> bad;
         int codes[8] = {0};
         for (int i = 0; i < num_clouds; ++i)
@@ -1752,7 +1754,7 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
                     if (want_edges)
                         VR_CUDA(cudaMemcpyAsync(dres->critical_edges[p], P->edges[p],
                                                 off[num_clouds] * 4 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-                    VR_CUDA(cudaStreamSynchronize(s));
+                    // stream-ordered: the caller reads the arrays on `stream` (no wait here)
                     memcpy(res->pair_offsets[p], off.data(), (num_clouds + 1) * sizeof(int64_t));
                     continue;
                 }

@@ -334,6 +334,20 @@ def _copies_done(stream):
         cur.synchronize()
 
 
+def _library_done(stream):
+    """A device result is written in the order of the call's stream; torch's
+    current stream, where its arrays are copied out, waits for it when the
+    two differ (an event wait on the device, not a host wait)."""
+    import torch
+    ptr = _stream_ptr(stream) or 0
+    cur = torch.cuda.current_stream()
+    if ptr != cur.cuda_stream:
+        if ptr:
+            cur.wait_stream(torch.cuda.ExternalStream(ptr))
+        else:
+            torch.cuda.synchronize()
+
+
 def _own(ptr, count, per, torch_dtype, cols):
     """A torch CUDA tensor (count, cols) copied from `count` records of `per`
     bytes at a library device pointer (a device-to-device copy)."""
@@ -418,6 +432,7 @@ def barcodes_batched_device(points, offsets, dmax=1, threshold=np.inf, flags=0, 
     code = lib.vr_barcodes_batched_device(ptr, offs.ctypes.data, len(offs) - 1, int(points.shape[1]), int(dmax),
                                           float(threshold), int(flags), _stream_ptr(stream), ctypes.byref(out))
     _check(code, "vr_barcodes_batched_device")
+    _library_done(stream)
     try:
         return DeviceBatchBarcodes(out.contents)
     finally:

@@ -164,3 +164,24 @@ def test_batched_output_larger_than_planned(vr):
         if i % 4 == 0:
             for p in range(2):
                 assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
+
+
+def test_batched_device_on_a_side_stream(vr):
+    """The device-resident batched result on a stream other than torch's
+    current one: the call returns without waiting for its copies, and the
+    binding makes the current stream wait before reading them; the values and
+    critical edges equal the host result's."""
+    import torch
+    circ = synth.circles(num=16, n=64, seed=11)
+    pts, offs = synth.pack(circ)
+    want = vr.barcodes_batched(pts, offs, dmax=1, flags=vr.VR_CRITICAL_EDGES)
+    x = torch.from_numpy(pts).cuda()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    got = vr.barcodes_batched_device(x, offs, dmax=1, flags=vr.VR_CRITICAL_EDGES, stream=side)
+    for p in range(2):
+        v = got.values[p].cpu().numpy()
+        assert np.array_equal(v[:, 0], want.pairs[p]["birth"]), p
+        assert np.array_equal(v[:, 1], want.pairs[p]["death"]), p
+        assert np.array_equal(got.edges[p].cpu().numpy(), want.critical_edges[p]), p
+        assert np.array_equal(got.offsets[p], want.offsets[p]), p
