@@ -375,9 +375,9 @@ __device__ void bit_add_list(const BitEng& E, const uint64_t* list, int len, int
 // lowest set bucket bit itself (a warp minimum over the words, no barrier)
 // and searches its share; the bucket and the result reach every thread
 // through the result slots after one barrier.  A bucket whose search finds
-// nothing is cleared and the next one searched.  `it` counts the searches
-// of the column: the result slot of search i is i mod 3, and slot i + 2 is
-// zeroed after search i's barrier, when search i - 1's slot has been read.
+// nothing is cleared and the next one searched.  `it` is the result slot
+// of the column's next search, counting searches mod 3: the slot of search i
+// + 2 (i - 1's) is zeroed after search i's barrier, when it has been read.
 template <bool SB, bool SR>
 __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, uint32_t& a_out, uint32_t& b_out,
                           uint32_t& w_out, uint32_t& t_out, int& c_out, bool& eq_aw, bool& eq_bw) {
@@ -394,7 +394,7 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
     const bool searcher = wid < sw;
     if (searcher && rp >= 0 && cp + H.dcnt <= 0) bit_clear_bucket(E, rp);
     for (;;) {
-        const int sl = it % 3;
+        const int sl = it;  // the slot of this search (it runs 0, 1, 2, 0, ...)
         if (searcher) {
             // the lowest non-empty word: eight words per lane loaded at once,
             // lane i taking words i, i + 32, ...; a batch with a set bit ends it
@@ -435,8 +435,9 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
         const int r = H.rr[sl];
         const uint32_t best = H.best[sl];
         const int cnt = H.cnt[sl];
-        if (threadIdx.x == 0) { H.best[(it + 2) % 3] = 0; H.cnt[(it + 2) % 3] = 0; }
-        ++it;
+        const int zs = sl == 0 ? 2 : sl - 1;  // the slot two searches on (the previous search's)
+        if (threadIdx.x == 0) { H.best[zs] = 0; H.cnt[zs] = 0; }
+        it = sl == 2 ? 0 : sl + 1;
         if (r < 0) return false;
         if (cnt) {
             const int g0 = E.ident ? r : (int)G[r], k = E.ident ? 1 : (int)G[r + 1] - g0;
