@@ -393,26 +393,39 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
     const int sw = (E.n + 31) >> 5;
     const bool searcher = wid < sw;
     if (searcher && rp >= 0 && cp + H.dcnt <= 0) bit_clear_bucket(E, rp);
+    // no bucket below the last pivot's holds a row (the pivot was the
+    // column's smallest row, and an addition's sum has no row below it, though
+    // the coboundaries of a finished column's generators may leave cancelled
+    // rows' bits there), so the search starts at that floor: its word, masked
+    // below it, is usually the answer, read by every lane at once
+    int fb = rp >= 0 ? rp : 0;
     for (;;) {
         const int sl = it;  // the slot of this search (it runs 0, 1, 2, 0, ...)
         if (searcher) {
-            // the lowest non-empty word: eight words per lane loaded at once,
-            // lane i taking words i, i + 32, ...; a batch with a set bit ends it
-            uint32_t lw = 0xFFFFFFFFu;
-            for (int base = 0; base < nw; base += 256) {
-                uint32_t v[8];
+            const int fw = fb >> 5;
+            uint32_t lw = 0xFFFFFFFFu, x0 = 0;
+            if (fw < nw) x0 = h0[fw] & (0xFFFFFFFFu << (fb & 31));
+            if (x0) {
+                lw = (uint32_t)fw;
+            } else {
+                // the lowest non-empty word above: eight words per lane loaded at
+                // once, lane i taking words i, i + 32, ... of a batch; a batch with
+                // a set bit ends it
+                for (int base = fw + 1; base < nw; base += 256) {
+                    uint32_t v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int i = base + u * 32 + lane;
-                    v[u] = i < nw ? h0[i] : 0u;
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = base + u * 32 + lane;
+                        v[u] = i < nw ? h0[i] : 0u;
+                    }
+#pragma unroll
+                    for (int u = 7; u >= 0; --u)
+                        if (v[u]) lw = (uint32_t)(base + u * 32 + lane);
+                    if (__any_sync(0xffffffffu, lw != 0xFFFFFFFFu)) break;
                 }
-#pragma unroll
-                for (int u = 7; u >= 0; --u)
-                    if (v[u]) lw = (uint32_t)(base + u * 32 + lane);
-                if (__any_sync(0xffffffffu, lw != 0xFFFFFFFFu)) break;
+                lw = __reduce_min_sync(0xffffffffu, lw);
             }
-            lw = __reduce_min_sync(0xffffffffu, lw);
-            const int r = lw == 0xFFFFFFFFu ? -1 : (int)(lw * 32 + __ffs(h0[lw]) - 1);
+            const int r = lw == 0xFFFFFFFFu ? -1 : (int)(lw * 32 + __ffs((int)lw == fw ? x0 : h0[lw]) - 1);
             if (threadIdx.x == 0) H.rr[sl] = r;
             if (r >= 0) {
                 const int g0 = E.ident ? r : (int)G[r], k = E.ident ? 1 : (int)G[r + 1] - g0;
@@ -453,7 +466,8 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
             if (threadIdx.x == 0) H.dcnt = 0;  // counted from the caller's next barrier on
             return true;
         }
-        if (searcher) bit_clear_bucket(E, r);  // bucket r is empty
+        if (searcher) bit_clear_bucket(E, r);  // bucket r is empty, and every one below it
+        fb = r + 1;
     }
 }
 
