@@ -401,6 +401,8 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
     int fb = rp >= 0 ? rp : 0;
     for (;;) {
         const int sl = it;  // the slot of this search (it runs 0, 1, 2, 0, ...)
+        int rs = -1;        // the searchers' bucket and its first edge, kept in registers
+        uint32_t abs0 = 0;
         if (searcher) {
             const int fw = fb >> 5;
             uint32_t lw = 0xFFFFFFFFu, x0 = 0;
@@ -427,9 +429,11 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
             }
             const int r = lw == 0xFFFFFFFFu ? -1 : (int)(lw * 32 + __ffs((int)lw == fw ? x0 : h0[lw]) - 1);
             if (threadIdx.x == 0) H.rr[sl] = r;
+            rs = r;
             if (r >= 0) {
                 const int g0 = E.ident ? r : (int)G[r], k = E.ident ? 1 : (int)G[r + 1] - g0;
                 const uint32_t ab0 = Es[g0];  // the bucket's first (usually only) edge
+                abs0 = ab0;
                 int found = 0;
                 for (int idx = threadIdx.x; idx < k * E.n; idx += sw * 32) {
                     const int ei = k == 1 ? 0 : idx / E.n, w = idx - ei * E.n;
@@ -445,7 +449,7 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
             }
         }
         bit_sync(E);
-        const int r = H.rr[sl];
+        const int r = searcher ? rs : H.rr[sl];
         const uint32_t best = H.best[sl];
         const int cnt = H.cnt[sl];
         const int zs = sl == 0 ? 2 : sl - 1;  // the slot two searches on (the previous search's)
@@ -455,7 +459,8 @@ __device__ bool bit_pivot(const BitEng& E, int rp, int cp, int& it, int& r_out, 
         if (cnt) {
             const int g0 = E.ident ? r : (int)G[r], k = E.ident ? 1 : (int)G[r + 1] - g0;
             const uint32_t t = best >> 10, w = (best >> 2) & 0xFFu;
-            uint32_t a = Es[g0] >> 8, b = Es[g0] & 0xFFu;
+            const uint32_t ab = searcher ? abs0 : Es[g0];
+            uint32_t a = ab >> 8, b = ab & 0xFFu;
             for (int ei = 1; ei < k && !(a != w && b != w && bit_tidx(a, b, w) == t); ++ei) {  // ties only
                 a = Es[g0 + ei] >> 8;
                 b = Es[g0 + ei] & 0xFFu;
