@@ -17,7 +17,8 @@
 //   4. drop cleared edges, sort the non-apparent ones into coboundary order;
 //   5. reduction (Algorithm 12): all columns once in parallel without
 //      additions, finalized in order by the prefix-minimum rule of reduce.cu,
-//      the rest in order by the front/back block engine;
+//      the rest in order by the bitmap engine (a bit per triangle, pivots
+//      through diameter buckets; see its section below);
 //   6. pairs sorted per cloud and appended to the output.
 // A cloud that outgrows a per-block buffer is flagged and recomputed by the
 // host through the single-cloud path.
@@ -43,7 +44,7 @@ constexpr int BMAXDIM = 16;
 constexpr int BLD = BMAXN;             // row stride of a cloud's square matrix
 constexpr int CCAP = 8192;             // non-apparent columns per cloud
 constexpr int HCAP = 16384;            // hash slots per cloud (power of two, >= 2 CCAP)
-constexpr int64_t BACKCAP = 1 << 20;   // back rows of the block engine per cloud (8 MB)
+constexpr int64_t BACKCAP = 1 << 20;   // per-cloud global scratch of the bitmap engine, in 8-byte units (8 MB)
 constexpr int EDGE_BITS = 15;          // C(256,2) - 1 < 2^15
 constexpr int TRI_BITS = 22;           // C(256,3) - 1 < 2^22
 constexpr int64_t POOLCAP = 1 << 15;   // stored reduced columns per cloud
@@ -1188,7 +1189,7 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
         __syncthreads();
         // 5a/5b. one round over the columns, one warp each, without additions:
         // it finds every pivot and settles, in order by the prefix-minimum rule,
-        // the columns whose pivot has no owner.  The rest go to the block engine
+        // the columns whose pivot has no owner.  The rest go to the bitmap engine
         // (measured faster on these clouds than more warp rounds).
         uint32_t* ucur = ulist;
         uint32_t* unext = ulist + CCAP;
@@ -1274,7 +1275,7 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
         if (A.prof && threadIdx.x == 0) atomicAdd(A.prof + 8, (unsigned long long)nu);
         unsigned long long adds = 0;
         if (nu > 0) {
-            // the block engine's space is the arena; the per-point buffers (points,
+            // the block engine's shared space is the arena; the per-point buffers (points,
             // clearing bits, tree, H0 records), no longer needed, the second arena
             constexpr uint32_t a2 = (uint32_t)offsetof(BatchSmem, pts);
             constexpr size_t a2b = offsetof(BatchSmem, h0) + sizeof(PairRec) * BMAXN - offsetof(BatchSmem, pts);
@@ -1722,7 +1723,7 @@ vr_status batched_impl(const float* pts, const int64_t* offsets, int32_t num_clo
             VR_CUDA(cudaMemcpy(pr, P->args.prof, sizeof pr, cudaMemcpyDeviceToHost));
             VR_CUDA(cudaMemcpy(st, P->args.stats, sizeof st, cudaMemcpyDeviceToHost));
             const char* names[8] = {"distances+threshold", "H0 tree + apparent", "H0 output", "clear+sort",
-                                    "first pass", "finalize", "block engine", "H1 output"};
+                                    "first pass", "finalize", "bitmap engine", "H1 output"};
             for (int i = 0; i < 8; ++i) fprintf(stderr, "[vr] batch %-20s %14llu cycles (all clouds, cumulative)\n", names[i], pr[i]);
             fprintf(stderr, "[vr] batch: candidates %llu apparent %llu columns %llu additions %llu, block-engine columns %llu\n",
                     st[0], st[1], st[2], st[3], pr[8]);
