@@ -1190,7 +1190,8 @@ __global__ void __launch_bounds__(HT, 2) k_batched(BatchArgs A) {
         // 5a/5b. one round over the columns, one warp each, without additions:
         // it finds every pivot and settles, in order by the prefix-minimum rule,
         // the columns whose pivot has no owner.  The rest go to the bitmap engine
-        // (measured faster on these clouds than more warp rounds).
+        // (measured faster on these clouds than warp rounds with additions: with
+        // up to 8 additions per column here, 4096 clouds 29.6 -> 31.1 ms).
         uint32_t* ucur = ulist;
         uint32_t* unext = ulist + CCAP;
         for (int i = threadIdx.x; i < m; i += HT) ucur[i] = (uint32_t)i;
