@@ -580,11 +580,12 @@ void run_p(const Ctx& c, const Emit& e, Workspace& ws, HostScratch& hs) {
         // Columns are finalized between rounds only, so a round that runs as
         // long as its longest column would keep columns it unblocks idle; a
         // cap of 64 additions (about 0.3 ms) keeps rounds short.  With at most
-        // eight unfinished columns few can be waiting, and rounds of up to 256
-        // additions save launches, state reloads and finalizations (measured on
-        // torus500: its two long dimension-1 columns, 10.0 -> 9.65 ms with the
-        // bound at four; dimension 2, 8.99 -> 8.85 ms with it at eight).
-        constexpr int budget_cap = 64, budget_cap_few = 256;
+        // eight unfinished columns few can be waiting, and longer rounds save
+        // launches, state reloads and finalizations (measured on torus500: up to
+        // 256 additions, its two long dimension-1 columns 10.0 -> 9.65 ms with the
+        // bound at four, dimension 2 8.99 -> 8.85 ms with it at eight; up to 1024,
+        // the step 19.70 -> 19.66 ms, three alternating pairs on one GPU).
+        constexpr int budget_cap = 64, budget_cap_few = 1024;
         int64_t stalled_adds = 0;  // additions granted to the first column since a column was last finalized
         cudaEvent_t ev[2] = {nullptr, nullptr};
         if (h.prof) { VR_CUDA(cudaEventCreate(&ev[0])); VR_CUDA(cudaEventCreate(&ev[1])); }
