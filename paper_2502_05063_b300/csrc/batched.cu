@@ -194,14 +194,19 @@ __device__ void emit_block(const BatchArgs& A, BatchSmem& M, int p, int cloud, c
 // threshold; a triangle of diameter rank r holds an edge of rank r, so the
 // rows of bucket r are found among the triangles {a, b, w} over the edges
 // (a, b) of rank r (one edge unless distances tie) and the third vertices
-// w.  One bit per bucket marks those that may hold a row (every warp finds
-// the lowest by a minimum over the words): a bucket's bit is set whenever
-// one of its rows flips, and cleared when its search finds nothing or when
-// the rows of the last pivot's bucket, counted, run out.
+// w.  One bit per bucket marks those that may hold a row: a bucket's bit is
+// set whenever one of its rows flips, and cleared when its search finds
+// nothing or when the rows of the last pivot's bucket, counted, run out.
+// No bucket below the last pivot's holds a row, so each search starts
+// there; the warps covering the vertices find the lowest set bit themselves
+// and search the bucket, with one barrier per search.
 // Owners follow the block engine's rule: the pivot of a finished column
 // (hash), else the apparent owner of Def 5.3.4 recomputed; a finished
 // column is added as its reduced form, the sum of the coboundaries of the
 // generators it records (its column of V).
+// The column loop runs on the warps covering the cloud's vertices plus one
+// that probes the hash, on a named barrier (bit_sync); the block's other
+// warps wait for the whole reduction at a block barrier.
 // Three variants by the cloud's size (bit_variant): the bitmap, the bucket
 // starts and the ranks in shared memory (n <= 128); the ranks only (n <=
 // 172); neither.  The head, the bucket bits and the edges by distance are
@@ -233,7 +238,7 @@ struct BitHead {
     uint32_t lo, hi;          // setup: the smallest and largest distance bits within the threshold
     int dcnt;                 // rows of the last pivot's bucket the last addition set (+1) or cleared (-1)
     int opos;                 // position of the finished column owning the pivot, or -1
-    int fail;
+    int fail;                 // a buffer was too small: the cloud goes to the single-cloud path
     unsigned long long poff;  // where the finished column's generators go in the pool
     int ws[HW + 1];
 };
