@@ -116,6 +116,36 @@ def test_lattice_ties(vr, n):
             assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, p)
 
 
+def test_sizes_where_the_kernel_switches_storage(vr):
+    """Clouds at each size where the batched kernel changes where it keeps
+    data: the dimension-1 engine's bitmap and bucket starts leave shared
+    memory above 128 points and its ranks above 172; steps 1-3 keep the
+    distances in shared memory up to 197 points.  A noisy circle (one long
+    cocycle column) and a uniform cube at each size, one batch; every cloud
+    equals the single-cloud path, and the circles at the four outer sizes
+    equal the oracle."""
+    sizes = [128, 129, 172, 173, 197, 198, 255, 256]
+    rng = np.random.default_rng(2025)
+    clouds = []
+    for n in sizes:
+        clouds.append(synth.circle(n, 1.0, 0.1, 2, g=rng).astype(np.float32))
+        clouds.append(rng.random((n, 3)).astype(np.float32))
+    pts, offs = synth.pack(clouds)
+    bb = vr.barcodes_batched(pts, offs, dmax=1)
+    assert bb.recomputed == 0
+    for i, c in enumerate(clouds):
+        single = vr.barcodes(points=c, dmax=1)
+        for p in range(2):
+            assert rows(bb.cloud(i, p)) == rows(single.pairs[p]), (i, len(c), p)
+    from oracle import pool
+    sample = [0, 2, 12, 14]
+    for i, dg in zip(sample, pool.diagrams([clouds[i] for i in sample], 1)):
+        for p in range(2):
+            want = [(float(np.float32(r["birth"])), float(np.float32(r["death"])) if np.isfinite(r["death"]) else math.inf,
+                     int(r["birth_cidx"]), int(r["death_cidx"])) for r in dg[p]]
+            assert rows(bb.cloud(i, p)) == want, (i, p)
+
+
 def test_recompute_when_generators_overflow(vr, monkeypatch):
     """With the per-cloud store of generators cut to 8 entries (read when a
     plan is built; this shape is used by no other test, so the plan is new),
