@@ -838,7 +838,7 @@ const char* vr_status_string(vr_status s) {
         case VR_ERR_OOM: return "out of memory";
         case VR_ERR_INDEX_OVERFLOW: return "simplex index or sort key overflows 64 bits";
         case VR_ERR_CUDA: return "CUDA runtime error";
-        case VR_ERR_TIMEOUT: return "bounded device wait timed out";
+        case VR_ERR_TIMEOUT: return "timeout (reserved: no entry point returns it)";
         case VR_ERR_INTERNAL: return "internal error";
     }
     return "unknown status";

@@ -128,7 +128,7 @@ def test_sizes_where_the_kernel_switches_storage(vr):
     rng = np.random.default_rng(2025)
     clouds = []
     for n in sizes:
-        clouds.append(synth.circle(n, 1.0, 0.1, 2, g=rng).astype(np.float32))
+        clouds.append(synth.circle(n, 1.0, 0.1, 3, g=rng).astype(np.float32))
         clouds.append(rng.random((n, 3)).astype(np.float32))
     pts, offs = synth.pack(clouds)
     bb = vr.barcodes_batched(pts, offs, dmax=1)
