@@ -486,6 +486,8 @@ static_assert(HSTAGE == 2 * HT, "a flushed stage holds two rows per thread");
 static_assert(FKEEP + HSTAGE <= FC, "a merge writes a front of FKEEP rows and a run of HSTAGE into FC");
 constexpr int REFILL_MAX = FC - HT;  // rows a refill may leave in the front
 static_assert(REFILL_MAX + HT <= FC, "a pass of generated rows (at most HT) fits after a refill");
+constexpr int pow2_ceil(int x) { return x <= 1 ? 1 : 2 * pow2_ceil((x + 1) / 2); }
+static_assert(pow2_ceil(REFILL_MAX) <= FC, "a refill sorts its rows in a front buffer, padded to a power of two");
 static_assert(HW <= 32, "block scans keep one total per warp in one warp");
 static_assert(FC < (1 << 16) && HSTAGE < (1 << 16), "merge splits pack two 16-bit indices");
 
