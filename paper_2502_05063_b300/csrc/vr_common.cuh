@@ -36,11 +36,11 @@ struct Error {
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 bool log_enabled();  // VR_LOG=1 in the environment: per-stage timings on stderr
 
-// Device-side error word written by kernels (bounded waits, capacity).
+// Device-side error word written by kernels (capacity, input and consistency checks).
 enum DeviceError : int {
     DEV_OK = 0,
     DEV_CAPACITY = 1,   // a scratch buffer was too small
-    DEV_TIMEOUT = 2,    // a bounded wait ran out
+    DEV_TIMEOUT = 2,    // reserved: no kernel waits on another, so none writes it
     DEV_INTERNAL = 3,   // a consistency check failed
     DEV_BAD_INPUT = 4,  // NaN / negative distance
 };
